@@ -1,0 +1,204 @@
+"""Seeded synthetic workloads for the EVD lattice Boltzmann step.
+
+This module only draws numbers: species tables, diffusivities, body forces and
+initial mole-fraction fields.  It contains none of the method's arithmetic, so
+both the CUDA path and the CPU oracle can be fed from it.  Every random number
+comes from SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom
+number generators", OOPSLA 2014) used as a counter-based generator: draw k of
+stream s is ``splitmix64(seed + (s * 2**40 + k + 1) * 0x9E3779B97F4A7C15)``.
+
+The paper has no public dataset.  The workloads below are stand-ins shaped like
+its cases: the Loschmidt tube with gravity of Sec. 4.1 (two gases, one in each
+half, periodic sides, impermeable ends) and a closed box relaxing to
+gravitational stratification.
+
+Field layout: ``x`` is float64 ``[ns][nz][ny][nx]`` (x fastest), mole fractions
+summing to 1 at every node.  ``n`` (total number density) is ``None`` for the
+uniform value 1.0.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED = 2504070591
+
+WALL_X = 0b000011
+WALL_Y = 0b001100
+WALL_Z = 0b110000
+
+D2Q9 = 0
+D3Q19 = 1
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(stream: int, count: int, seed: int = SEED, start: int = 0) -> np.ndarray:
+    """``count`` uint64 draws of stream ``stream`` beginning at index ``start``."""
+    with np.errstate(over="ignore"):
+        k = np.arange(start, start + count, dtype=np.uint64)
+        ctr = np.uint64(stream) * np.uint64(1 << 40) + k + np.uint64(1)
+        z = np.uint64(seed) + ctr * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(stream: int, count: int, seed: int = SEED) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits."""
+    return (splitmix64(stream, count, seed) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(stream: int, count: int, seed: int = SEED) -> np.ndarray:
+    """Standard normal draws by the Box-Muller transform of two uniform streams."""
+    u1 = uniform01(stream, count, seed)
+    u2 = uniform01(stream + 1, count, seed)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+@dataclass
+class Workload:
+    name: str
+    lattice: int
+    shape: tuple            # (nx, ny, nz)
+    wall_mask: int
+    M: tuple                # molar masses, non-decreasing (species 0 lightest)
+    D: np.ndarray           # [ns][ns] symmetric Maxwell-Stefan diffusivities, lattice units
+    tau1: float             # self relaxation time of the lightest species
+    g: tuple                # specific body force (gx, gy, gz), lattice units
+    steps: int              # number of time steps of the full case
+    x: np.ndarray = field(repr=False)   # [ns][nz][ny][nx]
+    n: np.ndarray | None = field(default=None, repr=False)
+    seed: int = SEED
+
+    @property
+    def ns(self) -> int:
+        return len(self.M)
+
+    @property
+    def Q(self) -> int:
+        return 9 if self.lattice == D2Q9 else 19
+
+    @property
+    def nsites(self) -> int:
+        nx, ny, nz = self.shape
+        return nx * ny * nz
+
+    def describe(self) -> dict:
+        nx, ny, nz = self.shape
+        return {
+            "workload": self.name,
+            "lattice": "D2Q9" if self.lattice == D2Q9 else "D3Q19",
+            "grid": [nx, ny] if self.lattice == D2Q9 else [nx, ny, nz],
+            "species": self.ns,
+            "molar_mass": list(self.M),
+            "g": list(self.g),
+            "tau1": self.tau1,
+            "walls": wall_names(self.wall_mask),
+            "seed": self.seed,
+        }
+
+
+def wall_names(mask: int) -> list:
+    names = ["x-", "x+", "y-", "y+", "z-", "z+"]
+    return [names[k] for k in range(6) if mask >> k & 1]
+
+
+def pair_diffusivities(ns: int, lo: float, hi: float, stream: int, seed: int = SEED) -> np.ndarray:
+    """Symmetric D_ij ~ U[lo, hi] for pairs (0,1),(0,2),...,(1,2),..., zero diagonal."""
+    npair = ns * (ns - 1) // 2
+    u = uniform01(stream, npair, seed)
+    D = np.zeros((ns, ns))
+    k = 0
+    for i in range(ns):
+        for j in range(i + 1, ns):
+            D[i, j] = D[j, i] = lo + (hi - lo) * u[k]
+            k += 1
+    return D
+
+
+def _renormalise(x: np.ndarray) -> np.ndarray:
+    return x / x.sum(axis=0, keepdims=True)
+
+
+def loschmidt_binary(nx: int = 4, ny: int = 256, steps: int = 2000) -> Workload:
+    """Binary Loschmidt tube without gravity: M = (1, 2), D_12 = 0.05, x_1 = 0.9
+    in rows y < ny/2 and 0.1 above, n = 1, walls at both ends of y, periodic x."""
+    x = np.empty((2, 1, ny, nx))
+    x[0, :, : ny // 2, :] = 0.9
+    x[0, :, ny // 2:, :] = 0.1
+    x[1] = 1.0 - x[0]
+    D = np.array([[0.0, 0.05], [0.05, 0.0]])
+    return Workload(f"loschmidt-binary-d2q9-{nx}x{ny}", D2Q9, (nx, ny, 1), WALL_Y,
+                    (1.0, 2.0), D, 1.0, (0.0, 0.0, 0.0), steps, x)
+
+
+GAS_A = (0.001, 0.299, 0.7)     # Sec. 4.1, gas A (x_1, x_2 = 1 - x_1 - x_3, x_3)
+GAS_B = (0.8, 0.199, 0.001)     # Sec. 4.1, gas B
+
+
+def loschmidt_ternary_gravity(nx: int = 64, ny: int = 1024, steps: int = 50000,
+                              g: float = 1e-6, seed: int = SEED) -> Workload:
+    """Ternary Loschmidt tube with gravity: M = (2, 28, 44), D_ij ~ U[0.02, 0.1],
+    gravity g along -y, gas A in the upper half and gas B in the lower half,
+    each mole fraction scaled by (1 + 0.01 u), u ~ U[-1, 1], then renormalised."""
+    ns = 3
+    x = np.empty((ns, 1, ny, nx))
+    for i in range(ns):
+        x[i, :, : ny // 2, :] = GAS_B[i]
+        x[i, :, ny // 2:, :] = GAS_A[i]
+    u = 2.0 * uniform01(2, x.size, seed).reshape(x.shape) - 1.0
+    x = _renormalise(x * (1.0 + 0.01 * u))
+    D = pair_diffusivities(ns, 0.02, 0.1, 1, seed)
+    return Workload(f"loschmidt-ternary-gravity-d2q9-{nx}x{ny}", D2Q9, (nx, ny, 1), WALL_Y,
+                    (2.0, 28.0, 44.0), D, 1.0, (0.0, -g, 0.0), steps, x, seed=seed)
+
+
+def stratification_3d(n: int = 256, steps: int = 20000, g: float = 2e-6,
+                      seed: int = SEED, shape: tuple | None = None) -> Workload:
+    """Closed D3Q19 box, walls on all six faces, M = (16, 28, 44),
+    D_ij ~ U[0.02, 0.1], gravity g along -y, x_i = (1/3)(1 + 0.01 N(0,1)) clipped
+    positive and renormalised."""
+    ns = 3
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    z = normal(4, ns * nx * ny * nz, seed).reshape(ns, nz, ny, nx)
+    x = np.maximum((1.0 / 3.0) * (1.0 + 0.01 * z), 1e-6)
+    x = _renormalise(x)
+    D = pair_diffusivities(ns, 0.02, 0.1, 3, seed)
+    return Workload(f"stratification-d3q19-{nx}x{ny}x{nz}", D3Q19, (nx, ny, nz),
+                    WALL_X | WALL_Y | WALL_Z, (16.0, 28.0, 44.0), D, 1.0, (0.0, -g, 0.0),
+                    steps, x, seed=seed)
+
+
+def random_mixture(lattice: int, shape: tuple, wall_mask: int, M: tuple,
+                   g: tuple = (0.0, 0.0, 0.0), tau1: float = 1.0,
+                   dlo: float = 0.02, dhi: float = 0.1, amp: float = 0.2,
+                   seed: int = SEED, stream: int = 10, n_amp: float = 0.0) -> Workload:
+    """Small generic case for parity tests: uniform mixture with seeded
+    mole-fraction noise of relative amplitude ``amp`` (and optionally a
+    number-density field 1 + n_amp * U[-1, 1])."""
+    ns = len(M)
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    u = uniform01(stream, ns * nx * ny * nz, seed).reshape(ns, nz, ny, nx)
+    x = _renormalise(np.full((ns, nz, ny, nx), 1.0 / ns) * (1.0 + amp * (2.0 * u - 1.0)))
+    D = pair_diffusivities(ns, dlo, dhi, stream + 1, seed)
+    nfield = None
+    if n_amp:
+        nfield = 1.0 + n_amp * (2.0 * uniform01(stream + 2, nx * ny * nz, seed).reshape(nz, ny, nx) - 1.0)
+    gg = tuple(g) + (0.0,) * (3 - len(g))
+    name = f"random-{'d2q9' if lattice == D2Q9 else 'd3q19'}-{nx}x{ny}x{nz}-ns{ns}"
+    return Workload(name, lattice, (nx, ny, nz), wall_mask, tuple(float(m) for m in M), D,
+                    tau1, gg, 0, x, nfield, seed)
+
+
+def by_name(name: str) -> Workload:
+    """The full-size workloads by short name."""
+    table = {
+        "loschmidt-binary": loschmidt_binary,
+        "loschmidt-ternary-gravity": loschmidt_ternary_gravity,
+        "stratification-3d": stratification_3d,
+    }
+    return table[name]()
