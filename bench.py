@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Throughput of the fused EVD lattice Boltzmann step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload stratification|tube] [--precision fp32|fp64|fp16]
+
+One bench step is one time step of the whole hot path (gather with
+interpolation and wall scheme, moments, tau_ij, collision with forcing) over
+the whole lattice.  The default workload is the 256^3 D3Q19 ternary closed box
+under gravity (the stratification case, the one whose working set exceeds L2,
+so HBM bandwidth is the bound and no L2 flush is needed between steps), FP32.
+
+Metric: species-site updates per second, GLUPS = N_species * sites * steps /
+time / 1e9, whole job over all ranks.  Every rank runs an independent replica
+(the path is single-GPU; there is no data-path collective), so scaling is weak.
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead (the paper publishes no
+implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_07059_gb300 import workloads as W  # noqa: E402
+
+METRIC = "species-site updates/s (GLUPS)"
+UNIT = "GLUPS"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch, from an
+# ncu capture of the kernel source with this digest (see profiles/).  A kernel
+# change changes the digest and the entry no longer applies.
+NCU_TRAFFIC = {}
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2504_07059_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(name: str, size: int = 256) -> W.Workload:
+    if name == "stratification":
+        return W.stratification_3d(n=size)
+    if name == "tube":
+        return W.loschmidt_ternary_gravity()
+    raise ValueError(name)
+
+
+def bytes_per_ssu(wl: W.Workload, precision: str) -> int:
+    """Algorithmic HBM bytes per species-site update: each population read
+    once and written once (ping-pong)."""
+    elem = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    return 2 * wl.Q * elem
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.device_id = device_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        loaded = sorted(sm)[len(sm) // 4:] or sm   # drop the idle tail of the window
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_device_id(torch, dev: int) -> str | None:
+    p = torch.cuda.get_device_properties(dev)
+    for attr in ("pci_bus_id",):
+        v = getattr(p, attr, None)
+        if v:
+            return str(v)
+    u = getattr(p, "uuid", None)
+    if u:
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    return None
+
+
+def time_oracle_sample(side: int, steps: int, warmup: int = 0) -> tuple[float, int, float]:
+    """The FP64 oracle on a side^3 copy of the stratification workload (same
+    recipe and seed).  Returns (seconds for ``steps`` steps, species-site
+    updates, seconds per step)."""
+    from oracle import oracle as O
+    wl = W.stratification_3d(shape=(side, side, side))
+    o = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+    o.init(wl.x)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return dt, wl.ns * wl.nsites * steps, dt / max(steps, 1)
+
+
+def cpu_baseline(budget_s: float = 15.0) -> dict:
+    """Bounded sample of the oracle: 32^3 copy of the workload, as many steps
+    as fit in about budget_s seconds (at least 2)."""
+    dt1, _, per = time_oracle_sample(32, 1)
+    steps = max(2, int(budget_s / max(per, 1e-6)))
+    dt, ssu, _ = time_oracle_sample(32, steps)
+    return {"value": ssu / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"stratification-d3q19-32x32x32 (same recipe and seed), {steps} steps, FP64, "
+                      f"single-threaded C, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # choose the sample cube so that warmup + steps end within about a minute
+    _, _, per16 = time_oracle_sample(16, 1)
+    total = args.steps + args.warmup
+    side = 16
+    for s in (32, 24, 16, 12, 8):
+        if per16 * (s / 16.0) ** 3 * total <= 60.0:
+            side = s
+            break
+    dt, ssu, _ = time_oracle_sample(side, args.steps, args.warmup)
+    value = ssu / dt / 1e9
+    wl = make_workload(args.workload, args.size)
+    out = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(wl.describe(), precision="fp64",
+                       sample=f"{side}x{side}x{side} copy of the workload (same recipe and seed)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"stratification-d3q19-{side}^3, {args.steps} steps after {args.warmup} "
+                                   f"warm-up, FP64 single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2504_07059_gb300 import build, evd
+    build.build()
+    wl = make_workload(args.workload, args.size)
+    prec = args.precision
+    ns, nsites = wl.ns, wl.nsites
+
+    stream = torch.cuda.current_stream(dev)
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, prec, stream)
+    # inputs resident in HBM before the timed region
+    x_dev = torch.from_numpy(np.ascontiguousarray(wl.x)).to(dev)
+    evd.evd_set_fields_device(sim.ctx, x_dev, None)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    evd.evd_step(sim.ctx, args.warmup)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = evd.evd_launch_count(sim.ctx)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_device_id(torch, local)) as clocks:
+        start.record(stream)
+        evd.evd_step(sim.ctx, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    evd.evd_check(sim.ctx)
+    launches = evd.evd_launch_count(sim.ctx) - launches0
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ssu_rank = ns * nsites * args.steps
+    value = world * ssu_rank / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant (only) kernel of the step: algorithmic bytes per
+    # launch over the average launch duration (one launch per step)
+    peak, peak_kind = measured_peaks()
+    bpl = bytes_per_ssu(wl, prec) * ns * nsites
+    achieved = bpl / (ms / args.steps * 1e-3) / 1e9
+    digest = kernel_digest()
+    traffic = NCU_TRAFFIC.get((digest, args.workload, prec))
+
+    # end to end through the public API with pinned host buffers: upload the
+    # initial mole fractions, run the same number of steps, read the mole
+    # fractions back
+    x_host = torch.from_numpy(np.ascontiguousarray(wl.x)).pin_memory()
+    out_host = torch.empty_like(x_host).pin_memory()
+    e2e_times = []
+    for _ in range(0 if args.no_e2e else 2):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        evd.evd_set_fields(sim.ctx, x_host, None)
+        evd.evd_step(sim.ctx, args.steps)
+        evd.evd_get_mole_fractions(sim.ctx, out_host)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = min(e2e_times) if e2e_times else float("nan")
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * ssu_rank / float(e2e_t.item()) / 1e9
+    h2d = x_host.numel() * 8
+    d2h = out_host.numel() * 8
+
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    sim.close()
+    if rank == 0:
+        cl = clocks.summary()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)"}[prec],
+            "data": "synthetic",
+            "config": dict(wl.describe(), precision=prec, parallelism=f"replicas{world}",
+                           l2="inputs larger than L2 (no flush needed)" if bpl > 129e6
+                           else "working set fits in L2 (HBM fraction not meaningful)"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": "k_step", "bytes_per_launch": bpl},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps_per_e2e_step": args.steps,
+                    "what": "evd_set_fields(pinned host x) + evd_step(steps) + "
+                            "evd_get_mole_fractions(pinned host)"},
+            "gpu_launches": launches,
+            "clocks": cl,
+        }
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["stratification", "tube"], default="stratification")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp16"], default="fp32")
+    ap.add_argument("--size", type=int, default=256, help="cube side of the stratification workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * evd.h -- C ABI of libevd, a GB300 (sm_103a) implementation of the forced
+ * explicit velocity-difference (EVD) multicomponent lattice Boltzmann step of
+ * Lourenco, Constantino & Tavares, "Forcing mass transfer approach in
+ * multicomponent miscible mixtures using the lattice Boltzmann method",
+ * Chem. Eng. Sci. 2025 (arXiv 2504.07059).
+ *
+ * One time step (Sec. 2 and 3 of the paper), per species i and lattice node x:
+ *   1. streaming with the species' own lattice speed c_i = sqrt(M_1/M_i)
+ *      (Eq. speed_DLS, Eq. discrete_velocity_DLS) and second-order spatial
+ *      interpolation back to the nodes (Eq. Second_order_spatial_interpolation),
+ *      closed at impermeable walls by the mass-conserving scheme of App. A and
+ *      periodic elsewhere;
+ *   2. moments rho_i, forced equilibrium velocity u_i^eq (Eq.
+ *      first_order_moment_force), mixture rho and u, number density n and ideal
+ *      pressure p = n M_1 c_s1^2 (Sec. 4.1);
+ *   3. cross relaxation times tau_ij from the Maxwell-Stefan diffusivities
+ *      (Eq. Luo&Girimaji_tau for two species, the closed forms of Sec. 4.1 for
+ *      three);
+ *   4. BGK self collision (Eq. BGK_self_collision) about f^{i(0)} (Eq. feqi0),
+ *      the velocity-difference cross collision (Eq. Cross_collision_Sirovich)
+ *      and the forcing term (Eq. CE_forcing_term_discretized) with
+ *      F_i = rho_i g, combined as in Eq. (LBE_forcing).
+ *
+ * Conventions.
+ *   - Sites are ordered x fastest: site = x + nx*(y + ny*z).  D2Q9 has nz = 1.
+ *   - Species are given in non-decreasing molar mass; species 0 is the lightest
+ *     and has lattice speed c = 1 (the paper's species 1).
+ *   - Lattice units throughout, dt = dx = 1.
+ *   - D2Q9 directions follow Eq. (discrete_velocity_DLS): 0 rest, 1 (+x),
+ *     2 (+y), 3 (-x), 4 (-y), 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y).
+ *     D3Q19 (an extension; the paper is two-dimensional): 0 rest, 1..6 =
+ *     +x -x +y -y +z -z, then (+x+y) (-x-y) (+x-y) (-x+y) (+x+z) (-x-z)
+ *     (+x-z) (-x+z) (+y+z) (-y-z) (+y-z) (-y+z).
+ *   - Host arrays are owned by the caller and copied.  Device arrays are
+ *     owned by the caller and must stay valid until the stream has consumed
+ *     them.  Every "_device" call is asynchronous on the context's stream;
+ *     every host-array readout synchronises that stream.
+ *   - No call aborts or exits.  Each returns a status; evd_last_error() gives
+ *     a message.  After EVD_ERR_CUDA the context must be destroyed.
+ *   - A context is not thread-safe; calls on one context must be serialised.
+ */
+#ifndef EVD_H
+#define EVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EVD_API_VERSION 1
+
+typedef enum {
+    EVD_OK = 0,
+    EVD_ERR_ARG = 1,       /* invalid argument or configuration                      */
+    EVD_ERR_CUDA = 2,      /* a CUDA runtime call failed; the context is unusable     */
+    EVD_ERR_UNSTABLE = 3,  /* a kernel saw rho_i <= 0, a NaN, or a non-positive tau_ij */
+    EVD_ERR_TIMEOUT = 4,   /* a bounded device-side wait gave up                      */
+    EVD_ERR_STATE = 5      /* call out of order (e.g. step before set_fields)         */
+} evd_status;
+
+typedef enum { EVD_D2Q9 = 0, EVD_D3Q19 = 1 } evd_lattice;
+
+/* Storage and arithmetic of the populations.
+ *   EVD_FP64       double storage, double arithmetic.
+ *   EVD_FP32       float storage of the deviation f - w_a rho_ref_i, float
+ *                  arithmetic (rho_ref_i = mean initial density of species i).
+ *   EVD_FP16_STORE half storage of the same deviation, float arithmetic.
+ * Per-species mass reductions are double in every mode. */
+typedef enum { EVD_FP64 = 0, EVD_FP32 = 1, EVD_FP16_STORE = 2 } evd_precision;
+
+/* wall_mask bits; a dimension is either periodic (both bits clear) or closed
+ * by impermeable walls at both ends (both bits set). */
+#define EVD_WALL_XM 0x01u
+#define EVD_WALL_XP 0x02u
+#define EVD_WALL_YM 0x04u
+#define EVD_WALL_YP 0x08u
+#define EVD_WALL_ZM 0x10u
+#define EVD_WALL_ZP 0x20u
+
+#define EVD_MAX_SPECIES 3
+
+typedef struct {
+    int lattice;          /* evd_lattice                                           */
+    int precision;        /* evd_precision                                         */
+    int nx, ny, nz;       /* nodes per dimension, >= 1; nz = 1 for D2Q9;          */
+                          /* nx*ny*nz < 2^31                                       */
+    unsigned wall_mask;   /* EVD_WALL_* bits                                       */
+} evd_grid;
+
+typedef struct {
+    int n_species;             /* 1 .. EVD_MAX_SPECIES                              */
+    const double* molar_mass;  /* [n_species], > 0, non-decreasing                  */
+    const double* diffusivity; /* [n_species*n_species], symmetric Maxwell-Stefan   */
+                               /* D_ij > 0 in lattice units; diagonal ignored        */
+    double tau1;               /* self relaxation time of species 0, > 1/2; the     */
+                               /* others follow from equal kinematic viscosity       */
+    double g[3];               /* specific body force, F_i = rho_i g (gravity)       */
+    unsigned flags;            /* reserved, must be 0                                */
+} evd_species;
+
+typedef struct evd_ctx evd_ctx;
+
+/* Library ABI version (EVD_API_VERSION). */
+int evd_version(void);
+
+/* Bytes of ONE population buffer for this configuration (the step ping-pongs
+ * between two).  Returns 0 for an invalid configuration. */
+size_t evd_required_bytes(const evd_grid* grid, const evd_species* species);
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream); all work of the context is ordered on it.
+ * The library allocates the two population buffers and small scratch.
+ * On failure *out is NULL and evd_last_error(NULL) describes the problem. */
+evd_status evd_create(const evd_grid* grid, const evd_species* species,
+                      void* cuda_stream, evd_ctx** out);
+
+/* As evd_create, but the two population buffers are caller-owned device
+ * memory of at least evd_required_bytes() each, 256-byte aligned, and must
+ * outlive the context.  Small scratch is still allocated by the library. */
+evd_status evd_create_with_buffers(const evd_grid* grid, const evd_species* species,
+                                   void* cuda_stream, void* pop_a, void* pop_b,
+                                   size_t bytes_each, evd_ctx** out);
+
+/* Change the stream later calls are ordered on. */
+evd_status evd_set_stream(evd_ctx* ctx, void* cuda_stream);
+
+/* Initial state (Sec. 4.1, 4.2): rho_i = x_i M_i n, zero velocities, and
+ * populations f = f^{i(0)} of Eq. (feqi0) with the equilibrium velocity
+ * replaced by u_i0 = -g dt/2, so that the first moments give u_i^eq = 0.
+ * x: [n_species][sites] mole fractions (> 0); n: [sites] total number
+ * density, or NULL for 1.  Resets the time to 0.  The host version
+ * synchronises; the device version is asynchronous apart from one small
+ * readback of the mean species densities. */
+evd_status evd_set_fields(evd_ctx* ctx, const double* x_host, const double* n_host);
+evd_status evd_set_fields_device(evd_ctx* ctx, const double* x_dev, const double* n_dev);
+
+/* Replace the state by arbitrary post-stream populations f_t, host array
+ * [n_species][Q][sites].  Keeps the time counter.  Synchronises. */
+evd_status evd_set_populations(evd_ctx* ctx, const double* f_host);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the stream. */
+evd_status evd_step(evd_ctx* ctx, long long nsteps);
+
+/* Observables of the current state f_t, asynchronously, into device arrays
+ * (any may be NULL):
+ *   x   [n_species][sites]      mole fraction x_i = rho_i/(n M_i)
+ *   rho [n_species][sites]      species density (Eq. zeroth_order_moment)
+ *   u   [D][sites]              mixture velocity (Eq. Sirovich_mixture_velocity)
+ *   ui  [n_species][D][sites]   species velocity u_i = u_i^eq - Theta_i/(2 rho_i)
+ *                               (Eq. CE_EQ83), D = 2 or 3 by lattice. */
+evd_status evd_readout_device(evd_ctx* ctx, double* x, double* rho, double* u, double* ui);
+
+/* Host-array readouts (synchronise the stream). */
+evd_status evd_get_mole_fractions(evd_ctx* ctx, double* x_host);
+evd_status evd_get_densities(evd_ctx* ctx, double* rho_host);
+evd_status evd_get_velocities(evd_ctx* ctx, double* u_mix_host, double* u_species_host);
+
+/* Per-species total mass sum_x rho_i(x) of the current state, reduced in
+ * double precision in a fixed order (bitwise reproducible run to run).
+ * The device version writes [n_species] doubles asynchronously. */
+evd_status evd_get_species_mass(evd_ctx* ctx, double* m_host);
+evd_status evd_species_mass_device(evd_ctx* ctx, double* m_dev);
+
+/* Post-stream populations f_t as doubles, host array [n_species][Q][sites]
+ * (a test hook; allocates a temporary device buffer of that size). */
+evd_status evd_get_populations(evd_ctx* ctx, double* f_host);
+
+/* Time steps taken since the last evd_set_fields. */
+long long evd_time(const evd_ctx* ctx);
+
+/* Synchronise and report the device error flag: EVD_ERR_UNSTABLE if any
+ * kernel since evd_set_fields saw a non-positive or NaN species density or a
+ * non-positive or non-finite cross relaxation time, else EVD_OK.  (tau_ij
+ * below 1/2 is a legitimate outcome of the ternary relation for trace
+ * species and is not flagged.) */
+evd_status evd_check(evd_ctx* ctx);
+
+/* Number of kernels this context has launched so far (launch accounting). */
+long long evd_launch_count(const evd_ctx* ctx);
+
+/* FP64 species-mass correction (not in the paper; a precision device for
+ * FP32/FP16 storage).  Every `every` steps the step kernel also reduces the
+ * per-species mass of f_t in double precision; the deficit from the initial
+ * masses (the target, computed in double at evd_set_fields) is re-injected in
+ * the next step as f_a += w_a (m0_i - m_i)/sites at every node.  0 turns it
+ * off.  Default: off for EVD_FP64, every 8 steps for EVD_FP32/EVD_FP16_STORE. */
+evd_status evd_set_mass_correction(evd_ctx* ctx, int every);
+
+/* The FP64 target masses [n_species] (initial species masses).  Synchronises. */
+evd_status evd_get_target_mass(evd_ctx* ctx, double* m_host);
+
+/* Release the context and all memory the library allocated for it. */
+evd_status evd_destroy(evd_ctx* ctx);
+
+/* Message of the last failed call on ctx, or of the last failed evd_create*
+ * on this thread when ctx is NULL.  Never NULL. */
+const char* evd_last_error(const evd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVD_H */

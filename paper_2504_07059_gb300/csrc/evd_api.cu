@@ -1,0 +1,715 @@
+// evd_api.cu -- the C ABI of libevd (declared in include/evd.h): context
+// management, validation, host-side constants, launches and readouts.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "evd.h"
+#include "evd_internal.h"
+
+using evd::HostParams;
+using evd::MAXS;
+
+namespace {
+
+constexpr int FLAG_MASS = 1, FLAG_RAW = 2;   // must match the device-side flags
+constexpr int BLOCK = 128;                   // must match the device-side block size
+constexpr long long PLANE_ALIGN = 64;        // elements; every plane starts 128-byte aligned
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct evd_ctx {
+    HostParams hp;
+    int lattice, precision, ns, Q, D;
+    int nx, ny, nz, nsites;
+    size_t elem;
+    long long pstride;
+    size_t buf_bytes;
+    void* buf[2];
+    bool own_bufs;
+    int cur;          // buf[cur] holds f*_t
+    bool prev_raw;    // buf[cur ^ 1] holds f_t itself (right after initialisation)
+    bool ready;
+    long long t;
+    cudaStream_t stream;
+    int device;
+    int nblocks;
+    double* mass_part;   // [nblocks][ns]
+    double* mass_out;    // [ns]
+    double* m_target;    // [ns] initial species masses (FP64)
+    double* corr[2];     // [ns] per-node mass corrections (two slots)
+    unsigned* err_flag;
+    void* small;         // one allocation holding the five arrays above
+    int mc_every;        // mass correction every k steps (0 = off)
+    int corr_pending;    // slot of a computed, not yet applied correction, or -1
+    int corr_applied;    // slot the last step applied (the readout applies it too), or -1
+    long long launches;  // kernels launched by this context
+    double* staging;     // device scratch for host transfers, grown on demand
+    size_t staging_bytes;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+evd_status fail(evd_ctx* c, evd_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+evd_status cuda_fail(evd_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, EVD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+    } while (0)
+
+size_t elem_size(int precision)
+{
+    return precision == EVD_FP64 ? 8 : (precision == EVD_FP32 ? 4 : 2);
+}
+
+// Checks every documented precondition; fills msg on failure.
+bool validate(const evd_grid* g, const evd_species* s, std::string& msg)
+{
+    if (!g || !s) { msg = "grid and species must not be NULL"; return false; }
+    if (g->lattice != EVD_D2Q9 && g->lattice != EVD_D3Q19) { msg = "unknown lattice"; return false; }
+    if (g->precision < EVD_FP64 || g->precision > EVD_FP16_STORE) { msg = "unknown precision"; return false; }
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) { msg = "grid extents must be >= 1"; return false; }
+    if (g->lattice == EVD_D2Q9 && g->nz != 1) { msg = "D2Q9 needs nz == 1"; return false; }
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    if (n >= (1LL << 31)) { msg = "nx*ny*nz must be below 2^31"; return false; }
+    if (g->wall_mask & ~0x3Fu) { msg = "unknown wall_mask bits"; return false; }
+    for (int k = 0; k < 3; ++k) {
+        const unsigned w = (g->wall_mask >> (2 * k)) & 3u;
+        if (w == 1u || w == 2u) { msg = "a dimension must be periodic or walled at both ends"; return false; }
+    }
+    if (g->lattice == EVD_D2Q9 && (g->wall_mask & 0x30u)) { msg = "D2Q9 has no z walls"; return false; }
+    if (s->n_species < 1 || s->n_species > EVD_MAX_SPECIES) { msg = "n_species must be 1..3"; return false; }
+    if (!s->molar_mass) { msg = "molar_mass is NULL"; return false; }
+    for (int i = 0; i < s->n_species; ++i) {
+        if (!(s->molar_mass[i] > 0.0) || !std::isfinite(s->molar_mass[i])) { msg = "molar masses must be > 0"; return false; }
+        if (i > 0 && s->molar_mass[i] < s->molar_mass[i - 1]) { msg = "molar masses must be non-decreasing"; return false; }
+    }
+    if (s->n_species > 1) {
+        if (!s->diffusivity) { msg = "diffusivity is NULL"; return false; }
+        const int N = s->n_species;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                const double a = s->diffusivity[i * N + j], b = s->diffusivity[j * N + i];
+                if (!(a > 0.0) || !std::isfinite(a)) { msg = "diffusivities must be > 0"; return false; }
+                if (std::fabs(a - b) > 1e-12 * std::fabs(a)) { msg = "diffusivity matrix must be symmetric"; return false; }
+            }
+    }
+    if (!(s->tau1 > 0.5) || !std::isfinite(s->tau1)) { msg = "tau1 must be > 1/2"; return false; }
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(s->g[k])) { msg = "g must be finite"; return false; }
+    if (g->lattice == EVD_D2Q9 && s->g[2] != 0.0) { msg = "D2Q9 needs g[2] == 0"; return false; }
+    if (s->flags != 0) { msg = "flags must be 0"; return false; }
+    return true;
+}
+
+long long plane_stride(const evd_grid* g)
+{
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    return (n + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
+}
+
+size_t buffer_bytes(const evd_grid* g, const evd_species* s)
+{
+    const int Q = g->lattice == EVD_D2Q9 ? 9 : 19;
+    return (size_t)plane_stride(g) * (size_t)(s->n_species * Q) * elem_size(g->precision);
+}
+
+// Constants of the scheme for this run (double precision).
+//   c_i = sqrt(M_1/M_i)                                  Eq. (speed_DLS)
+//   c_s,i^2 = c_i^2 / 3
+//   tau_i from (tau_i - 1/2) c_s,i^2 = (tau_1 - 1/2) c_s,1^2   (equal viscosity)
+//   1-D interpolation weights for a component s = c_i along the motion:
+//     upstream node  W(s;+1) = s(1+s)/2,  centre W(s;0) = 1 - s^2,
+//     downstream     W(s;-1) = -s(1-s)/2  (Eq. Second_order_spatial_interpolation)
+//   2 n^2 M_i M_j / (p dt) = n * 6 M_i M_j / M_1 with p = n M_1 c_s,1^2
+void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
+{
+    std::memset(&h, 0, sizeof(h));
+    h.lattice = g->lattice;
+    h.precision = g->precision;
+    h.ns = s->n_species;
+    h.nx = g->nx; h.ny = g->ny; h.nz = g->nz;
+    h.nsites = g->nx * g->ny * g->nz;
+    h.pstride = plane_stride(g);
+    for (int k = 0; k < 3; ++k) {
+        h.wall[k] = ((g->wall_mask >> (2 * k)) & 3u) ? 1 : 0;
+        h.g[k] = s->g[k];
+    }
+    if (g->lattice == EVD_D2Q9) { h.wl[0] = 4.0 / 9.0; h.wl[1] = 1.0 / 9.0; h.wl[2] = 1.0 / 36.0; }
+    else { h.wl[0] = 1.0 / 3.0; h.wl[1] = 1.0 / 18.0; h.wl[2] = 1.0 / 36.0; }
+    // Float arithmetic: constants whose sums must be exactly one (lattice
+    // weights, 1 - 1/tau + 1/tau, the 1-D interpolation weights) are put on
+    // the 2^-24 grid, where the float values are exact and the sums are
+    // exactly one.  Rounded independently they bias the species mass by up to
+    // ~3e-8 per step.
+    const bool on_grid = g->precision != EVD_FP64;
+    const double q = 16777216.0;
+    auto grid24 = [&](double v) { return on_grid ? std::nearbyint(v * q) / q : v; };
+    if (on_grid) {
+        const int n1 = g->lattice == EVD_D2Q9 ? 4 : 6, n2 = g->lattice == EVD_D2Q9 ? 4 : 12;
+        h.wl[1] = grid24(h.wl[1]);
+        h.wl[2] = grid24(h.wl[2]);
+        h.wl[0] = 1.0 - n1 * h.wl[1] - n2 * h.wl[2];
+    }
+    const double M1 = s->molar_mass[0];
+    const double cs2_1 = 1.0 / 3.0;
+    for (int i = 0; i < h.ns; ++i) {
+        const double Mi = s->molar_mass[i];
+        const double c = std::sqrt(M1 / Mi);
+        const double cs2 = c * c / 3.0;
+        const double tau = 0.5 + (s->tau1 - 0.5) * (cs2_1 / cs2);
+        h.M[i] = Mi;
+        h.Minv[i] = 1.0 / Mi;
+        h.c[i] = c;
+        h.unit[i] = (c == 1.0) ? 1 : 0;
+        h.inv_cs2[i] = 1.0 / cs2;
+        h.c_inv_cs2[i] = c / cs2;
+        h.tau_inv[i] = grid24(1.0 / tau);
+        h.omt[i] = on_grid ? 1.0 - h.tau_inv[i] : 1.0 - 1.0 / tau;
+        h.sfac[i] = 1.0 - 1.0 / (2.0 * tau);
+        h.w1[i][0] = c * (1.0 + c) / 2.0;
+        h.w1[i][1] = 1.0 - c * c;
+        h.w1[i][2] = -c * (1.0 - c) / 2.0;
+        if (on_grid) {
+            h.w1[i][0] = grid24(h.w1[i][0]);
+            h.w1[i][2] = grid24(h.w1[i][2]);
+            h.w1[i][1] = 1.0 - h.w1[i][0] - h.w1[i][2];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) h.w2[i][a][b] = h.w1[i][a] * h.w1[i][b];
+        for (int j = 0; j < h.ns; ++j) {
+            h.MM[i][j] = 6.0 * Mi * s->molar_mass[j] / M1;
+            h.iD[i][j] = (i == j) ? 0.0 : 1.0 / s->diffusivity[i * h.ns + j];
+        }
+    }
+}
+
+void set_reference(evd_ctx* c, const double* rho_ref)
+{
+    for (int i = 0; i < MAXS; ++i)
+        for (int k = 0; k < 3; ++k)
+            c->hp.ref[i][k] = (c->precision == EVD_FP64 || i >= c->ns) ? 0.0 : c->hp.wl[k] * rho_ref[i];
+}
+
+cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, const double* corr)
+{
+    const HostParams& h = c->hp;
+    double* mp = c->mass_part;
+    unsigned* e = c->err_flag;
+    cudaStream_t st = c->stream;
+    c->launches += 1;
+    switch (c->precision * 2 + c->lattice) {
+        case 0: return evd::Launch<0, 0>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 1: return evd::Launch<0, 1>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 2: return evd::Launch<1, 0>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 3: return evd::Launch<1, 1>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 4: return evd::Launch<2, 0>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 5: return evd::Launch<2, 1>::step(h, fin, fout, mp, e, flags, corr, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_readout(evd_ctx* c, const void* fin, int flags, double* x, double* rho, double* u,
+                           double* ui, double* fpop)
+{
+    const HostParams& h = c->hp;
+    double* mp = c->mass_part;
+    unsigned* e = c->err_flag;
+    cudaStream_t st = c->stream;
+    // f_t as the last step saw it includes the correction that step applied
+    const double* cr = (!(flags & FLAG_RAW) && c->corr_applied >= 0) ? c->corr[c->corr_applied] : nullptr;
+    c->launches += 1;
+    switch (c->precision * 2 + c->lattice) {
+        case 0: return evd::Launch<0, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 1: return evd::Launch<0, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 2: return evd::Launch<1, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 3: return evd::Launch<1, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 4: return evd::Launch<2, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 5: return evd::Launch<2, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(evd_ctx* c, const double* x, const double* n, const double* fsrc)
+{
+    const HostParams& h = c->hp;
+    void* prev = c->buf[c->cur ^ 1];
+    void* cur = c->buf[c->cur];
+    double* mp = c->mass_part;
+    unsigned* e = c->err_flag;
+    cudaStream_t st = c->stream;
+    c->launches += 1;
+    switch (c->precision * 2 + c->lattice) {
+        case 0: return evd::Launch<0, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 1: return evd::Launch<0, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 2: return evd::Launch<1, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 3: return evd::Launch<1, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 4: return evd::Launch<2, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 5: return evd::Launch<2, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Fixed-order sum of per-block partials [nblocks][ns]: thread t adds blocks
+// t, t+1024, ... in order, then a fixed binary tree.  Writes the totals to
+// out[ns], or, when target != nullptr, the per-node correction
+// (target_i - total_i) / nsites to out[ns].
+__global__ void __launch_bounds__(1024)
+evd_k_mass_finish(const double* __restrict__ part, int nblocks, int ns, const double* __restrict__ target,
+                  double inv_nsites, double* __restrict__ out)
+{
+    __shared__ double sm[1024];
+    for (int i = 0; i < ns; ++i) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += 1024) s += part[(long long)b * ns + i];
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 512; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[i] = target ? (target[i] - sm[0]) * inv_nsites : sm[0];
+        __syncthreads();
+    }
+}
+
+// Per-block partials of sum_x x_i M_i n (the initial species masses).
+__global__ void __launch_bounds__(128)
+evd_k_field_mass(const double* __restrict__ x, const double* __restrict__ nf, int nsites, int ns,
+                 double m0, double m1, double m2, double* __restrict__ part)
+{
+    __shared__ double sm[3][4];
+    const int node = blockIdx.x * 128 + threadIdx.x;
+    const bool active = node < nsites;
+    const double M[3] = {m0, m1, m2};
+    const double n = active ? (nf ? nf[node] : 1.0) : 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < ns; ++i) {
+        double v = active ? x[(long long)i * nsites + node] * M[i] * n : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sm[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        double t = 0.0;
+        for (int w = 0; w < 4; ++w) t += sm[threadIdx.x][w];
+        part[(long long)blockIdx.x * ns + threadIdx.x] = t;
+    }
+}
+
+namespace {
+
+evd_status ensure_staging(evd_ctx* c, size_t bytes)
+{
+    if (c->staging_bytes >= bytes) return EVD_OK;
+    if (c->staging) cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+    CK(c, cudaMalloc((void**)&c->staging, bytes));
+    c->staging_bytes = bytes;
+    return EVD_OK;
+}
+
+evd_status finish_mass(evd_ctx* c, double* out, const double* target = nullptr)
+{
+    c->launches += 1;
+    evd_k_mass_finish<<<1, 1024, 0, c->stream>>>(c->mass_part, c->nblocks, c->ns, target,
+                                                 1.0 / (double)c->nsites, out);
+    CK(c, cudaGetLastError());
+    return EVD_OK;
+}
+
+evd_status create_common(const evd_grid* grid, const evd_species* species, void* stream, void* pa,
+                         void* pb, size_t bytes_each, evd_ctx** out)
+{
+    if (!out) return fail(nullptr, EVD_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    std::string msg;
+    if (!validate(grid, species, msg)) return fail(nullptr, EVD_ERR_ARG, msg);
+    evd_ctx* c = new evd_ctx();
+    c->lattice = grid->lattice;
+    c->precision = grid->precision;
+    c->ns = species->n_species;
+    c->Q = grid->lattice == EVD_D2Q9 ? 9 : 19;
+    c->D = grid->lattice == EVD_D2Q9 ? 2 : 3;
+    c->nx = grid->nx; c->ny = grid->ny; c->nz = grid->nz;
+    c->nsites = grid->nx * grid->ny * grid->nz;
+    c->elem = elem_size(grid->precision);
+    c->pstride = plane_stride(grid);
+    c->buf_bytes = buffer_bytes(grid, species);
+    c->stream = (cudaStream_t)stream;
+    c->nblocks = (c->nsites + BLOCK - 1) / BLOCK;
+    fill_params(c->hp, grid, species);
+    double zero[MAXS] = {0, 0, 0};
+    set_reference(c, zero);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    if (pa || pb) {
+        if (!pa || !pb || pa == pb) { delete c; return fail(nullptr, EVD_ERR_ARG, "need two distinct buffers"); }
+        if (bytes_each < c->buf_bytes) { delete c; return fail(nullptr, EVD_ERR_ARG, "buffers too small"); }
+        if (((uintptr_t)pa | (uintptr_t)pb) & 255u) { delete c; return fail(nullptr, EVD_ERR_ARG, "buffers must be 256-byte aligned"); }
+        c->buf[0] = pa; c->buf[1] = pb; c->own_bufs = false;
+    } else {
+        c->own_bufs = true;
+        for (int b = 0; b < 2; ++b) {
+            e = cudaMalloc(&c->buf[b], c->buf_bytes);
+            if (e != cudaSuccess) {
+                if (b == 1) cudaFree(c->buf[0]);
+                delete c;
+                return cuda_fail(nullptr, e, "cudaMalloc(populations)");
+            }
+        }
+    }
+    const size_t part_bytes = ((size_t)c->nblocks * c->ns * sizeof(double) + 255) / 256 * 256;
+    e = cudaMalloc(&c->small, part_bytes + 5 * 256);
+    if (e != cudaSuccess) {
+        if (c->own_bufs) { cudaFree(c->buf[0]); cudaFree(c->buf[1]); }
+        delete c;
+        return cuda_fail(nullptr, e, "cudaMalloc(scratch)");
+    }
+    c->mass_part = (double*)c->small;
+    c->mass_out = (double*)((char*)c->small + part_bytes);
+    c->m_target = (double*)((char*)c->small + part_bytes + 256);
+    c->corr[0] = (double*)((char*)c->small + part_bytes + 512);
+    c->corr[1] = (double*)((char*)c->small + part_bytes + 768);
+    c->err_flag = (unsigned*)((char*)c->small + part_bytes + 1024);
+    c->corr_pending = c->corr_applied = -1;
+    c->mc_every = (c->precision == EVD_FP64) ? 0 : 8;
+    e = cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) {
+        evd_destroy(c);
+        return cuda_fail(nullptr, e, "cudaMemsetAsync");
+    }
+    *out = c;
+    return EVD_OK;
+}
+
+evd_status readout_to_host(evd_ctx* c, double* x_h, double* rho_h, double* u_h, double* ui_h)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    const size_t n = (size_t)c->nsites;
+    const size_t sx = x_h ? c->ns * n : 0, sr = rho_h ? c->ns * n : 0, su = u_h ? c->D * n : 0,
+                 sui = ui_h ? c->ns * c->D * n : 0;
+    evd_status s = ensure_staging(c, (sx + sr + su + sui + 1) * sizeof(double));
+    if (s != EVD_OK) return s;
+    double* d = c->staging;
+    double *dx = x_h ? d : nullptr, *dr = rho_h ? d + sx : nullptr, *du = u_h ? d + sx + sr : nullptr,
+           *dui = ui_h ? d + sx + sr + su : nullptr;
+    s = evd_readout_device(c, dx, dr, du, dui);
+    if (s != EVD_OK) return s;
+    if (x_h) CK(c, cudaMemcpyAsync(x_h, dx, sx * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (rho_h) CK(c, cudaMemcpyAsync(rho_h, dr, sr * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u_h) CK(c, cudaMemcpyAsync(u_h, du, su * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (ui_h) CK(c, cudaMemcpyAsync(ui_h, dui, sui * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return evd_check(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int evd_version(void) { return EVD_API_VERSION; }
+
+size_t evd_required_bytes(const evd_grid* grid, const evd_species* species)
+{
+    std::string msg;
+    if (!validate(grid, species, msg)) return 0;
+    return buffer_bytes(grid, species);
+}
+
+evd_status evd_create(const evd_grid* grid, const evd_species* species, void* cuda_stream, evd_ctx** out)
+{
+    return create_common(grid, species, cuda_stream, nullptr, nullptr, 0, out);
+}
+
+evd_status evd_create_with_buffers(const evd_grid* grid, const evd_species* species, void* cuda_stream,
+                                   void* pop_a, void* pop_b, size_t bytes_each, evd_ctx** out)
+{
+    if (!pop_a || !pop_b) {
+        if (out) *out = nullptr;
+        return fail(nullptr, EVD_ERR_ARG, "pop_a and pop_b must not be NULL");
+    }
+    return create_common(grid, species, cuda_stream, pop_a, pop_b, bytes_each, out);
+}
+
+evd_status evd_set_stream(evd_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return EVD_OK;
+}
+
+evd_status evd_set_fields_device(evd_ctx* c, const double* x_dev, const double* n_dev)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!x_dev) return fail(c, EVD_ERR_ARG, "x must not be NULL");
+    DeviceGuard dg(c->device);
+    // initial species masses sum_x x_i M_i n in FP64: the target of the mass
+    // correction and, for deviation storage, the reference densities
+    c->launches += 1;
+    evd_k_field_mass<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, c->hp.M[0],
+                                                        c->hp.M[1], c->hp.M[2], c->mass_part);
+    CK(c, cudaGetLastError());
+    evd_status s0 = finish_mass(c, c->m_target);
+    if (s0 != EVD_OK) return s0;
+    if (c->precision != EVD_FP64) {
+        double m[MAXS] = {0, 0, 0}, ref[MAXS] = {0, 0, 0};
+        CK(c, cudaMemcpyAsync(m, c->m_target, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < c->ns; ++i) {
+            if (!(m[i] > 0.0)) return fail(c, EVD_ERR_ARG, "initial species mass must be > 0");
+            ref[i] = m[i] / c->nsites;
+        }
+        set_reference(c, ref);
+    }
+    CK(c, cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned), c->stream));
+    c->cur = 0;
+    CK(c, launch_init(c, x_dev, n_dev, nullptr));
+    c->prev_raw = true;
+    c->ready = true;
+    c->corr_pending = c->corr_applied = -1;
+    c->t = 0;
+    return EVD_OK;
+}
+
+evd_status evd_set_fields(evd_ctx* c, const double* x_host, const double* n_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!x_host) return fail(c, EVD_ERR_ARG, "x must not be NULL");
+    const size_t n = (size_t)c->nsites;
+    for (size_t k = 0; k < c->ns * n; ++k)
+        if (!(x_host[k] > 0.0) || !std::isfinite(x_host[k])) return fail(c, EVD_ERR_ARG, "mole fractions must be > 0");
+    if (n_host)
+        for (size_t k = 0; k < n; ++k)
+            if (!(n_host[k] > 0.0) || !std::isfinite(n_host[k])) return fail(c, EVD_ERR_ARG, "number density must be > 0");
+    DeviceGuard dg(c->device);
+    evd_status s = ensure_staging(c, (c->ns * n + n) * sizeof(double));
+    if (s != EVD_OK) return s;
+    CK(c, cudaMemcpyAsync(c->staging, x_host, c->ns * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (n_host)
+        CK(c, cudaMemcpyAsync(c->staging + c->ns * n, n_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    s = evd_set_fields_device(c, c->staging, n_host ? c->staging + c->ns * n : nullptr);
+    if (s != EVD_OK) return s;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return evd_check(c);
+}
+
+evd_status evd_set_populations(evd_ctx* c, const double* f_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!f_host) return fail(c, EVD_ERR_ARG, "f must not be NULL");
+    DeviceGuard dg(c->device);
+    const size_t n = (size_t)c->nsites, total = (size_t)c->ns * c->Q * n;
+    double m[MAXS] = {0, 0, 0}, ref[MAXS] = {0, 0, 0};
+    for (int i = 0; i < c->ns; ++i) {
+        for (size_t k = 0; k < (size_t)c->Q * n; ++k) m[i] += f_host[(size_t)i * c->Q * n + k];
+        if (!(m[i] > 0.0)) return fail(c, EVD_ERR_ARG, "species mass must be > 0");
+        ref[i] = m[i] / n;
+    }
+    if (c->precision != EVD_FP64) set_reference(c, ref);
+    CK(c, cudaMemcpyAsync(c->m_target, m, c->ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->corr_pending = c->corr_applied = -1;
+    evd_status s = ensure_staging(c, total * sizeof(double));
+    if (s != EVD_OK) return s;
+    CK(c, cudaMemcpyAsync(c->staging, f_host, total * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (!c->ready) CK(c, cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned), c->stream));
+    CK(c, launch_init(c, nullptr, nullptr, c->staging));
+    c->prev_raw = true;
+    c->ready = true;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return evd_check(c);
+}
+
+evd_status evd_step(evd_ctx* c, long long nsteps)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, EVD_ERR_ARG, "nsteps must be >= 0");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    for (long long k = 0; k < nsteps; ++k) {
+        // every mc_every steps the step kernel also reduces the species masses
+        // of f_t; the deficit from the FP64 targets is re-injected uniformly
+        // in the next step
+        const bool measure = c->mc_every > 0 && ((c->t + 1) % c->mc_every == 0);
+        const int apply = c->corr_pending;
+        CK(c, launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], measure ? FLAG_MASS : 0,
+                          apply >= 0 ? c->corr[apply] : nullptr));
+        c->corr_applied = apply;
+        c->corr_pending = -1;
+        if (measure) {
+            const int slot = (apply == 0) ? 1 : 0;
+            evd_status s = finish_mass(c, c->corr[slot], c->m_target);
+            if (s != EVD_OK) return s;
+            c->corr_pending = slot;
+        }
+        c->cur ^= 1;
+        c->prev_raw = false;
+        c->t += 1;
+    }
+    return EVD_OK;
+}
+
+evd_status evd_readout_device(evd_ctx* c, double* x, double* rho, double* u, double* ui)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    CK(c, launch_readout(c, c->buf[c->cur ^ 1], c->prev_raw ? FLAG_RAW : 0, x, rho, u, ui, nullptr));
+    return finish_mass(c, c->mass_out);
+}
+
+evd_status evd_get_mole_fractions(evd_ctx* c, double* x_host)
+{
+    if (!x_host) return fail(c, EVD_ERR_ARG, "x must not be NULL");
+    return readout_to_host(c, x_host, nullptr, nullptr, nullptr);
+}
+
+evd_status evd_get_densities(evd_ctx* c, double* rho_host)
+{
+    if (!rho_host) return fail(c, EVD_ERR_ARG, "rho must not be NULL");
+    return readout_to_host(c, nullptr, rho_host, nullptr, nullptr);
+}
+
+evd_status evd_get_velocities(evd_ctx* c, double* u_mix_host, double* u_species_host)
+{
+    if (!u_mix_host && !u_species_host) return fail(c, EVD_ERR_ARG, "no output given");
+    return readout_to_host(c, nullptr, nullptr, u_mix_host, u_species_host);
+}
+
+evd_status evd_species_mass_device(evd_ctx* c, double* m_dev)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!m_dev) return fail(c, EVD_ERR_ARG, "m must not be NULL");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    CK(c, launch_readout(c, c->buf[c->cur ^ 1], c->prev_raw ? FLAG_RAW : 0, nullptr, nullptr, nullptr,
+                         nullptr, nullptr));
+    return finish_mass(c, m_dev);
+}
+
+evd_status evd_get_species_mass(evd_ctx* c, double* m_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!m_host) return fail(c, EVD_ERR_ARG, "m must not be NULL");
+    evd_status s = evd_species_mass_device(c, c->mass_out);
+    if (s != EVD_OK) return s;
+    DeviceGuard dg(c->device);
+    CK(c, cudaMemcpyAsync(m_host, c->mass_out, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return evd_check(c);
+}
+
+evd_status evd_get_populations(evd_ctx* c, double* f_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!f_host) return fail(c, EVD_ERR_ARG, "f must not be NULL");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    const size_t total = (size_t)c->ns * c->Q * c->nsites;
+    double* tmp = nullptr;
+    CK(c, cudaMalloc((void**)&tmp, total * sizeof(double)));
+    cudaError_t e = launch_readout(c, c->buf[c->cur ^ 1], c->prev_raw ? FLAG_RAW : 0, nullptr, nullptr, nullptr,
+                                   nullptr, tmp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "evd_get_populations");
+    return evd_check(c);
+}
+
+long long evd_time(const evd_ctx* c) { return c ? c->t : -1; }
+
+evd_status evd_check(evd_ctx* c)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    unsigned flag = 0;
+    CK(c, cudaMemcpyAsync(&flag, c->err_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (flag) {
+        std::string m = "unstable state:";
+        if (flag & 1u) m += " non-positive or NaN species density;";
+        if (flag & 2u) m += " cross relaxation time tau_ij <= 1/2 or NaN;";
+        return fail(c, EVD_ERR_UNSTABLE, m);
+    }
+    return EVD_OK;
+}
+
+long long evd_launch_count(const evd_ctx* c) { return c ? c->launches : -1; }
+
+evd_status evd_set_mass_correction(evd_ctx* c, int every)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (every < 0) return fail(c, EVD_ERR_ARG, "every must be >= 0");
+    c->mc_every = every;
+    if (every == 0) c->corr_pending = -1;
+    return EVD_OK;
+}
+
+evd_status evd_get_target_mass(evd_ctx* c, double* m_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!m_host) return fail(c, EVD_ERR_ARG, "m must not be NULL");
+    if (!c->ready) return fail(c, EVD_ERR_STATE, "set_fields has not been called");
+    DeviceGuard dg(c->device);
+    CK(c, cudaMemcpyAsync(m_host, c->m_target, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return EVD_OK;
+}
+
+evd_status evd_destroy(evd_ctx* c)
+{
+    if (!c) return EVD_OK;
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->own_bufs) {
+        cudaFree(c->buf[0]);
+        cudaFree(c->buf[1]);
+    }
+    if (c->small) cudaFree(c->small);
+    if (c->staging) cudaFree(c->staging);
+    delete c;
+    return EVD_OK;
+}
+
+const char* evd_last_error(const evd_ctx* c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

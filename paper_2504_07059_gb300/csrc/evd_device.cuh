@@ -1,0 +1,684 @@
+// evd_device.cuh -- device code of the fused EVD lattice Boltzmann step.
+//
+// One thread owns one lattice node and all of its species: the cross
+// collision couples the species at a node, so every population of the node
+// must be in registers before the collision.  The step is the "pull" form of
+// the paper's time step: the stored buffer holds post-collision populations
+// f*_{t-1}; a launch gathers them with the second-order interpolation of
+// Eq. (Second_order_spatial_interpolation) (plus the App. A wall terms at
+// wall-adjacent nodes) into f_t, computes the moments, the cross relaxation
+// times and the collision of Eq. (LBE_forcing), and writes f*_t.
+//
+// Layout in HBM: structure of arrays, one plane per (species, direction),
+// plane p = i*Q + a at element offset p * pstride, x fastest inside a plane,
+// pstride rounded up to 64 elements so every plane starts 128-byte aligned.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "evd_internal.h"
+
+namespace evd {
+
+constexpr int BLOCK = 128;
+
+enum : int { F_MASS = 1, F_RAW = 2 };          // kernel flags
+enum : unsigned { ERR_RHO = 1u, ERR_TAU = 2u };  // device error bits
+
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// ---------------------------------------------------------------- lattices
+template <int LAT> struct Lat;
+template <> struct Lat<0> { static constexpr int Q = 9, D = 2; };
+template <> struct Lat<1> { static constexpr int Q = 19, D = 3; };
+
+// Unit direction vectors; D2Q9 in the order of Eq. (discrete_velocity_DLS).
+template <int LAT>
+__host__ __device__ constexpr int ev(int a, int k)
+{
+    if (LAT == 0) {
+        constexpr int E[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+        return E[a][k];
+    } else {
+        constexpr int E[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return E[a][k];
+    }
+}
+
+template <int LAT>
+__host__ __device__ constexpr int opp(int a)
+{
+    int b = 0;
+    for (int c = 0; c < Lat<LAT>::Q; ++c)
+        if (ev<LAT>(c, 0) == -ev<LAT>(a, 0) && ev<LAT>(c, 1) == -ev<LAT>(a, 1) &&
+            ev<LAT>(c, 2) == -ev<LAT>(a, 2))
+            b = c;
+    return b;
+}
+
+// weight class = number of non-zero components: 0 rest, 1 axis, 2 diagonal
+template <int LAT>
+__host__ __device__ constexpr int wclass(int a)
+{
+    return (ev<LAT>(a, 0) != 0) + (ev<LAT>(a, 1) != 0) + (ev<LAT>(a, 2) != 0);
+}
+
+// --------------------------------------------------------------- parameters
+// Per-run constants, computed on the host in double and cast to T.
+template <typename T>
+struct Params {
+    int nx, ny, nz, nsites;
+    long long pstride;
+    int wall[3];           // 1 if that dimension is closed by walls at both ends
+    int unit[MAXS];        // species moves exactly one node per step (c == 1)
+    T c[MAXS];             // lattice speed c_i = sqrt(M_1 / M_i)
+    T inv_cs2[MAXS];       // 1 / c_s,i^2 = 3 / c_i^2
+    T c_inv_cs2[MAXS];     // c_i / c_s,i^2 = 3 / c_i
+    T tau_inv[MAXS];       // 1 / tau_i
+    T omt[MAXS];           // 1 - 1/tau_i
+    T sfac[MAXS];          // 1 - 1/(2 tau_i)
+    T Minv[MAXS];          // 1 / M_i
+    T M[MAXS];
+    T MM[MAXS][MAXS];      // 2 n^2 M_i M_j / (p dt) = n * MM_ij  (p = n M_1 / 3)
+    T iD[MAXS][MAXS];      // 1 / D_ij
+    T g[3];                // specific body force
+    T w1[MAXS][3];         // 1-D interpolation weights: [upstream, centre, downstream]
+    T w2[MAXS][3][3];      // products w1[a] * w1[b]
+    T wl[3];               // lattice weight per class (rest, axis, diagonal)
+    T ref[MAXS][3];        // deviation reference per class: wl[class] * rho_ref_i
+};
+
+template <typename T>
+inline Params<T> to_params(const HostParams& h)
+{
+    Params<T> p;
+    p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.nsites = h.nsites;
+    p.pstride = h.pstride;
+    for (int k = 0; k < 3; ++k) { p.wall[k] = h.wall[k]; p.g[k] = (T)h.g[k]; p.wl[k] = (T)h.wl[k]; }
+    for (int i = 0; i < MAXS; ++i) {
+        p.unit[i] = h.unit[i];
+        p.c[i] = (T)h.c[i]; p.inv_cs2[i] = (T)h.inv_cs2[i]; p.c_inv_cs2[i] = (T)h.c_inv_cs2[i];
+        p.tau_inv[i] = (T)h.tau_inv[i]; p.omt[i] = (T)h.omt[i]; p.sfac[i] = (T)h.sfac[i];
+        p.Minv[i] = (T)h.Minv[i]; p.M[i] = (T)h.M[i];
+        for (int j = 0; j < MAXS; ++j) { p.MM[i][j] = (T)h.MM[i][j]; p.iD[i][j] = (T)h.iD[i][j]; }
+        for (int a = 0; a < 3; ++a) {
+            p.w1[i][a] = (T)h.w1[i][a];
+            p.ref[i][a] = (T)h.ref[i][a];
+            for (int b = 0; b < 3; ++b) p.w2[i][a][b] = (T)h.w2[i][a][b];
+        }
+    }
+    return p;
+}
+
+// --------------------------------------------------------- storage codecs
+// Raw double storage, or the deviation f - w_a rho_ref_i in float / half.
+template <typename S> struct Codec;
+template <> struct Codec<double> {
+    static constexpr bool DEV = false;
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct Codec<float> {
+    static constexpr bool DEV = true;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Codec<__half> {
+    static constexpr bool DEV = true;
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// ------------------------------------------------------------- neighbours
+// off[k][o+1]: element offset of the node at o in {-1,0,+1} along dimension k
+// (periodic wrap; 0 when that node is solid).  lo/hi: the node touches the
+// low/high wall of dimension k.
+struct Nbr {
+    int off[3][3];
+    bool lo[3], hi[3];
+    bool any_wall;
+};
+
+template <typename T>
+__device__ __forceinline__ Nbr neighbours(const Params<T>& p, int node)
+{
+    Nbr nb;
+    const int nxy = p.nx * p.ny;
+    const int crd[3] = {node % p.nx, (node / p.nx) % p.ny, node / nxy};
+    const int stride[3] = {1, p.nx, nxy};
+    const int ext[3] = {p.nx, p.ny, p.nz};
+    nb.any_wall = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool at_lo = crd[k] == 0, at_hi = crd[k] == ext[k] - 1;
+        nb.lo[k] = p.wall[k] && at_lo;
+        nb.hi[k] = p.wall[k] && at_hi;
+        nb.any_wall |= nb.lo[k] | nb.hi[k];
+        nb.off[k][1] = 0;
+        nb.off[k][0] = at_lo ? (p.wall[k] ? 0 : (ext[k] - 1) * stride[k]) : -stride[k];
+        nb.off[k][2] = at_hi ? (p.wall[k] ? 0 : -(ext[k] - 1) * stride[k]) : stride[k];
+    }
+    return nb;
+}
+
+// 1-D weight index of source offset o along a dimension whose unit velocity
+// component is e (!= 0): upstream (o == -e) 0, centre 1, downstream 2.
+__host__ __device__ constexpr int widx(int o, int e) { return o == -e ? 0 : (o == 0 ? 1 : 2); }
+
+// -------------------------------------------------------------- the gather
+// Interior node: f_a(O) = sum over the 1/3/9 stencil nodes O + o of
+// W(o) f*_a(O + o), the tensor product of 1-D weights along the (one or two)
+// dimensions direction a moves in.
+template <int LAT, int I, int A, typename S, typename T>
+__device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __restrict__ fin, int node,
+                                             const Nbr& nb)
+{
+    constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
+    const S* plane = fin + (long long)(I * Lat<LAT>::Q + A) * p.pstride + node;
+    T acc;
+    if constexpr (ex == 0 && ey == 0 && ez == 0) {
+        acc = (T)Codec<S>::ld(plane);
+    } else {
+        if (p.unit[I]) {
+            acc = (T)Codec<S>::ld(plane + nb.off[0][1 - ex] + nb.off[1][1 - ey] + nb.off[2][1 - ez]);
+        } else {
+            constexpr int k1 = ex != 0 ? 0 : (ey != 0 ? 1 : 2);
+            constexpr int k2 = (ex != 0 && ey != 0) ? 1 : (((ex != 0 || ey != 0) && ez != 0) ? 2 : -1);
+            constexpr int e1 = ev<LAT>(A, k1);
+            acc = (T)0;
+            if constexpr (k2 < 0) {
+#pragma unroll
+                for (int o1 = -1; o1 <= 1; ++o1)
+                    acc += p.w1[I][widx(o1, e1)] * (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1]);
+            } else if constexpr (std::is_same<T, double>::value) {
+                constexpr int e2 = ev<LAT>(A, k2);
+#pragma unroll
+                for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+                    for (int o1 = -1; o1 <= 1; ++o1)
+                        acc += p.w2[I][widx(o1, e1)][widx(o2, e2)] *
+                               (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
+            } else {
+                // float arithmetic: two 1-D passes, so that the effective 2-D
+                // weights are products of 1-D weights that sum to exactly one
+                constexpr int e2 = ev<LAT>(A, k2);
+#pragma unroll
+                for (int o2 = -1; o2 <= 1; ++o2) {
+                    T row = (T)0;
+#pragma unroll
+                    for (int o1 = -1; o1 <= 1; ++o1)
+                        row += p.w1[I][widx(o1, e1)] *
+                               (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
+                    acc += p.w1[I][widx(o2, e2)] * row;
+                }
+            }
+        }
+    }
+    if constexpr (Codec<S>::DEV) acc += p.ref[I][wclass<LAT>(A)];
+    return acc;
+}
+
+// Push weight of direction B from a node X to X + d (the interpolation read as
+// a redistribution of each streamed value, as App. A does).
+template <int LAT, int B, typename T>
+__device__ __forceinline__ T push_weight(const Params<T>& p, int I, int dx, int dy, int dz)
+{
+    const int d[3] = {dx, dy, dz};
+    T w = (T)1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int e = ev<LAT>(B, k);
+        if (e != 0) w *= p.w1[I][d[k] == e ? 0 : (d[k] == 0 ? 1 : 2)];
+    }
+    return w;
+}
+
+// App. A lumping at a wall-adjacent node O for direction B leaving O: weight
+// bound for a solid node O + d stays at O, in the opposite direction when B
+// heads into the crossed wall(s) (e_B . d_s > 0, d_s the crossing components
+// of d), and in B itself otherwise (ties at edges and corners included).
+// Returns the weight kept in B (into_self) or sent to the opposite of B.
+template <int LAT, int B, typename T>
+__device__ __forceinline__ T lumped(const Params<T>& p, int I, const Nbr& nb, bool into_self)
+{
+    constexpr int ex = ev<LAT>(B, 0), ey = ev<LAT>(B, 1), ez = ev<LAT>(B, 2);
+    T acc = (T)0;
+#pragma unroll
+    for (int dz = (ez ? -1 : 0); dz <= (ez ? 1 : 0); ++dz)
+#pragma unroll
+        for (int dy = (ey ? -1 : 0); dy <= (ey ? 1 : 0); ++dy)
+#pragma unroll
+            for (int dx = (ex ? -1 : 0); dx <= (ex ? 1 : 0); ++dx) {
+                const int d[3] = {dx, dy, dz};
+                bool crossed = false;
+                int dot = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const bool cr = (d[k] == 1 && nb.hi[k]) || (d[k] == -1 && nb.lo[k]);
+                    crossed |= cr;
+                    if (cr) dot += ev<LAT>(B, k) * d[k];
+                }
+                if (crossed && ((dot > 0) != into_self)) acc += push_weight<LAT, B>(p, I, dx, dy, dz);
+            }
+    return acc;
+}
+
+// Wall-adjacent node: only fluid stencil nodes contribute, plus the lumped
+// weight of O's own populations in directions a and its opposite.
+template <int LAT, int I, int A, typename S, typename T>
+__device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict__ fin, int node,
+                                         const Nbr& nb)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
+    constexpr int AB = opp<LAT>(A);
+    const S* plane = fin + (long long)(I * Q + A) * p.pstride + node;
+    const T ref = Codec<S>::DEV ? p.ref[I][wclass<LAT>(A)] : (T)0;
+    T acc = (T)0;
+#pragma unroll
+    for (int oz = (ez ? -1 : 0); oz <= (ez ? 1 : 0); ++oz)
+#pragma unroll
+        for (int oy = (ey ? -1 : 0); oy <= (ey ? 1 : 0); ++oy)
+#pragma unroll
+            for (int ox = (ex ? -1 : 0); ox <= (ex ? 1 : 0); ++ox) {
+                const bool solid = (ox == -1 && nb.lo[0]) || (ox == 1 && nb.hi[0]) ||
+                                   (oy == -1 && nb.lo[1]) || (oy == 1 && nb.hi[1]) ||
+                                   (oz == -1 && nb.lo[2]) || (oz == 1 && nb.hi[2]);
+                if (!solid) {
+                    const T w = push_weight<LAT, A>(p, I, -ox, -oy, -oz);  // from O + o to O: d = -o
+                    acc += w * ((T)Codec<S>::ld(plane + nb.off[0][ox + 1] + nb.off[1][oy + 1] +
+                                                nb.off[2][oz + 1]) + ref);
+                }
+            }
+    if constexpr (ex != 0 || ey != 0 || ez != 0) {
+        const T ls = lumped<LAT, A>(p, I, nb, true);
+        const T lo = lumped<LAT, AB>(p, I, nb, false);
+        if (ls != (T)0) acc += ls * ((T)Codec<S>::ld(plane) + ref);
+        if (lo != (T)0) acc += lo * ((T)Codec<S>::ld(fin + (long long)(I * Q + AB) * p.pstride + node) + ref);
+    }
+    return acc;
+}
+
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restrict__ fin, int node,
+                                           const Nbr& nb, T (&f)[NS][Lat<LAT>::Q])
+{
+    constexpr int Q = Lat<LAT>::Q;
+    if (!nb.any_wall) {
+        static_for<0, NS>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                f[I][A] = gather_interior<LAT, I, A>(p, fin, node, nb);
+            });
+        });
+    } else {
+        static_for<0, NS>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                f[I][A] = gather_wall<LAT, I, A>(p, fin, node, nb);
+            });
+        });
+    }
+}
+
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict__ fin, int node,
+                                         T (&f)[NS][Lat<LAT>::Q])
+{
+    constexpr int Q = Lat<LAT>::Q;
+    static_for<0, NS>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        static_for<0, Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            T v = (T)Codec<S>::ld(fin + (long long)(I * Q + A) * p.pstride + node);
+            if constexpr (Codec<S>::DEV) v += p.ref[I][wclass<LAT>(A)];
+            f[I][A] = v;
+        });
+    });
+}
+
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fout, int node,
+                                          const T (&f)[NS][Lat<LAT>::Q])
+{
+    constexpr int Q = Lat<LAT>::Q;
+    static_for<0, NS>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        static_for<0, Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            T v = f[I][A];
+            if constexpr (Codec<S>::DEV) v -= p.ref[I][wclass<LAT>(A)];
+            Codec<S>::st(fout + (long long)(I * Q + A) * p.pstride + node, v);
+        });
+    });
+}
+
+// e_a . v with the unit vector of direction A (compile-time signs)
+template <int LAT, int A, typename T>
+__device__ __forceinline__ T edot(const T (&v)[3])
+{
+    T s = (T)0;
+    if constexpr (ev<LAT>(A, 0) == 1) s += v[0];
+    if constexpr (ev<LAT>(A, 0) == -1) s -= v[0];
+    if constexpr (ev<LAT>(A, 1) == 1) s += v[1];
+    if constexpr (ev<LAT>(A, 1) == -1) s -= v[1];
+    if constexpr (ev<LAT>(A, 2) == 1) s += v[2];
+    if constexpr (ev<LAT>(A, 2) == -1) s -= v[2];
+    return s;
+}
+
+// -------------------------------------------------- moments and relaxation
+template <int NS, typename T>
+struct NodeState {
+    T rho[NS];
+    T ueq[NS][3];
+    T u[3];
+    T V[NS][3];   // sum_j (rho_j / rho) (u_i^eq - u_j^eq) / tau_ij = Theta_i / rho_i
+    T rho_mix, n;
+};
+
+// Moments (Eq. zeroth_order_moment, first_order_moment_force with F_i =
+// rho_i g, Eq. Sirovich_mixture_density and _velocity), n = sum rho_i/M_i and
+// the cross relaxation rates 1/tau_ij of Eq. (relation_tauij_diff_coeff):
+// Eq. (Luo&Girimaji_tau) for two species and the Sec. 4.1 closed forms for
+// three, written for 1/tau_ij.
+template <int LAT, int NS, typename T>
+__device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat<LAT>::Q],
+                                        NodeState<NS, T>& s, unsigned& err)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    s.rho_mix = (T)0;
+    s.n = (T)0;
+    static_for<0, NS>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        T r = (T)0, j[3] = {(T)0, (T)0, (T)0};
+        static_for<0, Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            const T v = f[I][A];
+            r += v;
+            if constexpr (ev<LAT>(A, 0) == 1) j[0] += v;
+            if constexpr (ev<LAT>(A, 0) == -1) j[0] -= v;
+            if constexpr (ev<LAT>(A, 1) == 1) j[1] += v;
+            if constexpr (ev<LAT>(A, 1) == -1) j[1] -= v;
+            if constexpr (ev<LAT>(A, 2) == 1) j[2] += v;
+            if constexpr (ev<LAT>(A, 2) == -1) j[2] -= v;
+        });
+        if (!(r > (T)0)) err |= ERR_RHO;
+        const T rinv = (T)1 / r;
+        s.rho[I] = r;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s.ueq[I][k] = p.c[I] * j[k] * rinv + (T)0.5 * p.g[k];
+        s.rho_mix += r;
+        s.n += r * p.Minv[I];
+    });
+    const T rinv_m = (T)1 / s.rho_mix;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T acc = (T)0;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc += s.rho[i] * s.ueq[i][k];
+        s.u[k] = acc * rinv_m;
+    }
+    // X_ij = 1/tau_ij
+    T X[MAXS][MAXS] = {};
+    if constexpr (NS == 2) {
+        const T A12 = (s.rho[0] + s.rho[1]) * p.iD[0][1] + s.n * p.MM[0][1];
+        const T B12 = (T)2 * s.rho_mix * p.iD[0][1];
+        X[0][1] = X[1][0] = B12 / A12;
+    } else if constexpr (NS == 3) {
+        const T r1 = s.rho[0], r2 = s.rho[1], r3 = s.rho[2];
+        const T A12 = (r1 + r2) * p.iD[0][1] + s.n * p.MM[0][1];
+        const T A13 = (r1 + r3) * p.iD[0][2] + s.n * p.MM[0][2];
+        const T A23 = (r2 + r3) * p.iD[1][2] + s.n * p.MM[1][2];
+        const T B12 = (T)2 * s.rho_mix * p.iD[0][1];
+        const T B13 = (T)2 * s.rho_mix * p.iD[0][2];
+        const T B23 = (T)2 * s.rho_mix * p.iD[1][2];
+        const T rA13 = (T)1 / A13;
+        const T X23 = (B23 - r1 * B13 * rA13 * p.iD[1][2]) /
+                      (A23 - r1 * r2 * rA13 * p.iD[0][2] * p.iD[1][2]);
+        const T X12 = (B12 - r3 * X23 * p.iD[0][1]) / A12;
+        const T X13 = (B13 - r2 * X23 * p.iD[0][2]) * rA13;
+        X[0][1] = X[1][0] = X12;
+        X[0][2] = X[2][0] = X13;
+        X[1][2] = X[2][1] = X23;
+    }
+    // tau_ij < 1/2 is a legitimate outcome of the relation (it happens for
+    // trace species); only a non-positive or non-finite tau_ij is an error.
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NS; ++j)
+            if (!(X[i][j] > (T)0) || !isfinite(X[i][j])) err |= ERR_TAU;
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T acc = (T)0;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                if (j != i) acc += s.rho[j] * X[i][j] * (s.ueq[i][k] - s.ueq[j][k]);
+            s.V[i][k] = acc * rinv_m;
+        }
+}
+
+// Collision of Eq. (LBE_forcing) in place, f <- f*:
+//   f* = f - (f - f^(0))/tau_i + sum_j Omega^ij + (1 - 1/(2 tau_i)) S
+// with f^(0) = [1 + (e-u).(u_i^eq-u)/c_s^2] f^eq (Eq. feqi0),
+//      sum_j Omega^ij = -(f^eq/c_s^2)(e-u).V_i (Eq. Cross_collision_Sirovich),
+//      S = w [e/c_s^2 + (ee - c_s^2 I).u/c_s^4].F_i (Eq. CE_forcing_term_discretized),
+// rearranged to  f* = (1 - 1/tau) f + f^eq [1/tau + (e-u).a/c_s^2] + (1-1/(2tau)) S,
+//                a  = (u_i^eq - u)/tau - V_i.
+template <int LAT, int NS, typename T>
+__device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
+                                        const NodeState<NS, T>& s)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const T usq = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+    const T ug = s.u[0] * p.g[0] + s.u[1] * p.g[1] + s.u[2] * p.g[2];
+    T av[NS][3], Bc[NS], U2[NS], wr[NS][3], sr[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        T ua = (T)0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            av[i][k] = (s.ueq[i][k] - s.u[k]) * p.tau_inv[i] - s.V[i][k];
+            ua += s.u[k] * av[i][k];
+        }
+        Bc[i] = p.tau_inv[i] - p.inv_cs2[i] * ua;
+        U2[i] = (T)1 - (T)0.5 * p.inv_cs2[i] * usq;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wr[i][c] = p.wl[c] * s.rho[i];
+        sr[i] = s.rho[i] * p.inv_cs2[i] * p.sfac[i];
+    }
+    static_for<0, Q>([&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        constexpr int C = wclass<LAT>(A);
+        const T eu = edot<LAT, A>(s.u);
+        const T eg = edot<LAT, A>(p.g);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const T ea = edot<LAT, A>(av[i]);
+            const T t1 = p.c_inv_cs2[i] * eu;                       // e.u / c_s^2
+            const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
+            const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);
+            const T S = p.wl[C] * sr[i] * fma(p.c[i] * eg, (T)1 + t1, -ug);
+            f[i][A] = fma(p.omt[i], f[i][A], fma(feq, B, S));
+        }
+    });
+}
+
+// ------------------------------------------------------ block reductions
+// Per-block partial of sum rho_i in double; a fixed-order second pass
+// (mass_finish) makes the total reproducible.
+template <int NS, typename T>
+__device__ __forceinline__ void block_mass(const T (&rho)[NS], bool active, double* __restrict__ part)
+{
+    __shared__ double sm[NS][BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        double v = active ? (double)rho[i] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sm[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < BLOCK / 32; ++w) t += sm[threadIdx.x][w];
+        part[(long long)blockIdx.x * NS + threadIdx.x] = t;
+    }
+}
+
+// ----------------------------------------------------------------- kernels
+// One time step: gather f*_{t-1} -> f_t, collide -> f*_t.
+// Uniform re-injection of a species-mass deficit: f_a += w_a * corr_i keeps
+// the moments' shape and adds corr_i to rho_i at every node.
+template <int LAT, int NS, typename T>
+__device__ __forceinline__ void add_correction(const Params<T>& p, const double* __restrict__ corr,
+                                               T (&f)[NS][Lat<LAT>::Q])
+{
+    static_for<0, NS>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const T ci = (T)__ldg(corr + I);
+        static_for<0, Lat<LAT>::Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            f[I][A] = fma(p.wl[wclass<LAT>(A)], ci, f[I][A]);
+        });
+    });
+}
+
+template <int LAT, int NS, typename S, typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
+       double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
+       const double* __restrict__ corr)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    const bool active = node < p.nsites;
+    T f[NS][Q];
+    NodeState<NS, T> s;
+    unsigned err = 0;
+    if (active) {
+        const Nbr nb = neighbours(p, node);
+        gather_all<LAT, NS>(p, fin, node, nb, f);
+        if (corr) add_correction<LAT, NS>(p, corr, f);
+        moments<LAT, NS>(p, f, s, err);
+        collide<LAT, NS>(p, f, s);
+        store_all<LAT, NS>(p, fout, node, f);
+        if (err) atomicOr(err_flag, err);
+    }
+    if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
+}
+
+// Observables of f_t: gathered from f*_{t-1}, or read directly when the
+// buffer holds f_t itself (F_RAW, right after initialisation).
+template <int LAT, int NS, typename S, typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __restrict__ x,
+          double* __restrict__ rho, double* __restrict__ u, double* __restrict__ ui,
+          double* __restrict__ fpop, double* __restrict__ mass_part, unsigned* __restrict__ err_flag,
+          const double* __restrict__ corr)
+{
+    constexpr int Q = Lat<LAT>::Q, D = Lat<LAT>::D;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    const bool active = node < p.nsites;
+    T f[NS][Q];
+    NodeState<NS, T> s;
+    unsigned err = 0;
+    if (active) {
+        if (flags & F_RAW) {
+            load_raw<LAT, NS>(p, fin, node, f);
+        } else {
+            const Nbr nb = neighbours(p, node);
+            gather_all<LAT, NS>(p, fin, node, nb, f);
+            if (corr) add_correction<LAT, NS>(p, corr, f);   // as the last step saw f_t
+        }
+        moments<LAT, NS>(p, f, s, err);
+        const long long ns_ = p.nsites;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            if (x) x[i * ns_ + node] = (double)(s.rho[i] * p.Minv[i]) / (double)s.n;
+            if (rho) rho[i * ns_ + node] = (double)s.rho[i];
+#pragma unroll
+            for (int k = 0; k < D; ++k)   // u_i = u_i^eq - Theta_i/(2 rho_i), Eq. (CE_EQ83)
+                if (ui) ui[(i * D + k) * ns_ + node] = (double)(s.ueq[i][k] - (T)0.5 * s.V[i][k]);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            if (u) u[k * ns_ + node] = (double)s.u[k];
+        if (fpop) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+#pragma unroll
+                for (int a = 0; a < Q; ++a) fpop[(i * Q + a) * ns_ + node] = (double)f[i][a];
+        }
+        if (err) atomicOr(err_flag, err);
+    }
+    block_mass<NS>(s.rho, active, mass_part);
+}
+
+// Initial state f_0 into fprev (kept for the time-0 readout) and its collision
+// f*_0 into fcur.  f_0 comes from mole fractions x and number density n
+// (rho_i = x_i M_i n, f = w rho_i [1 + e.u_i0 / c_s^2], u_i0 = -g/2), or from
+// caller populations fsrc [ns][Q][nsites] when fsrc != nullptr.
+template <int LAT, int NS, typename S, typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_init(const Params<T> p, const double* __restrict__ xf, const double* __restrict__ nf,
+       const double* __restrict__ fsrc, S* __restrict__ fprev, S* __restrict__ fcur,
+       double* __restrict__ mass_part, unsigned* __restrict__ err_flag)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    const bool active = node < p.nsites;
+    T f[NS][Q];
+    NodeState<NS, T> s;
+    unsigned err = 0;
+    if (active) {
+        const long long ns_ = p.nsites;
+        if (fsrc) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+#pragma unroll
+                for (int a = 0; a < Q; ++a) f[i][a] = (T)fsrc[(i * Q + a) * ns_ + node];
+        } else {
+            const T n = nf ? (T)nf[node] : (T)1;
+            static_for<0, NS>([&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                const T r = (T)xf[I * ns_ + node] * p.M[I] * n;
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int A = decltype(ac)::value;
+                    const T eg = edot<LAT, A>(p.g);
+                    f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
+                });
+            });
+        }
+        store_all<LAT, NS>(p, fprev, node, f);
+        moments<LAT, NS>(p, f, s, err);
+        collide<LAT, NS>(p, f, s);
+        store_all<LAT, NS>(p, fcur, node, f);
+        if (err) atomicOr(err_flag, err);
+    }
+    block_mass<NS>(s.rho, active, mass_part);
+}
+
+}  // namespace evd

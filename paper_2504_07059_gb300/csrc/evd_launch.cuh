@@ -1,0 +1,78 @@
+// evd_launch.cuh -- (lattice, species count) dispatch of the kernel templates
+// for one storage type S and arithmetic type T.
+#pragma once
+
+#include "evd_device.cuh"
+
+namespace evd {
+
+#define EVD_DISPATCH(KERNEL, ...)                                                    \
+    if (h.lattice != LAT) return cudaErrorInvalidValue;                              \
+    switch (h.ns) {                                                                  \
+        case 1: KERNEL<LAT, 1, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
+        case 2: KERNEL<LAT, 2, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
+        case 3: KERNEL<LAT, 3, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
+        default: return cudaErrorInvalidValue;                                       \
+    }
+
+template <int LAT, typename S, typename T>
+cudaError_t dispatch_step(const HostParams& h, const void* fin, void* fout, double* mass_part,
+                          unsigned* err, int flags, const double* corr, cudaStream_t st)
+{
+    const Params<T> p = to_params<T>(h);
+    const int grid = grid_blocks(h, BLOCK);
+    if (grid == 0) return cudaSuccess;
+    EVD_DISPATCH(k_step, p, (const S*)fin, (S*)fout, mass_part, err, flags, corr)
+    return cudaGetLastError();
+}
+
+template <int LAT, typename S, typename T>
+cudaError_t dispatch_readout(const HostParams& h, const void* fin, int flags, double* x, double* rho,
+                             double* u, double* ui, double* fpop, double* mass_part, unsigned* err,
+                             const double* corr, cudaStream_t st)
+{
+    const Params<T> p = to_params<T>(h);
+    const int grid = grid_blocks(h, BLOCK);
+    if (grid == 0) return cudaSuccess;
+    EVD_DISPATCH(k_readout, p, (const S*)fin, flags, x, rho, u, ui, fpop, mass_part, err, corr)
+    return cudaGetLastError();
+}
+
+template <int LAT, typename S, typename T>
+cudaError_t dispatch_init(const HostParams& h, const double* x, const double* n, const double* fsrc,
+                          void* fprev, void* fcur, double* mass_part, unsigned* err, cudaStream_t st)
+{
+    const Params<T> p = to_params<T>(h);
+    const int grid = grid_blocks(h, BLOCK);
+    if (grid == 0) return cudaSuccess;
+    EVD_DISPATCH(k_init, p, x, n, fsrc, (S*)fprev, (S*)fcur, mass_part, err)
+    return cudaGetLastError();
+}
+
+#undef EVD_DISPATCH
+
+}  // namespace evd
+
+#define EVD_DEFINE_LAUNCHERS(PREC, LAT, S, T)                                                              \
+    namespace evd {                                                                                   \
+    template <>                                                                                       \
+    cudaError_t Launch<PREC, LAT>::step(const HostParams& h, const void* fin, void* fout, double* mp,      \
+                                   unsigned* err, int flags, const double* corr, cudaStream_t st)     \
+    {                                                                                                 \
+        return dispatch_step<LAT, S, T>(h, fin, fout, mp, err, flags, corr, st);                      \
+    }                                                                                                 \
+    template <>                                                                                       \
+    cudaError_t Launch<PREC, LAT>::readout(const HostParams& h, const void* fin, int flags, double* x,     \
+                                      double* rho, double* u, double* ui, double* fpop, double* mp,   \
+                                      unsigned* err, const double* corr, cudaStream_t st)             \
+    {                                                                                                 \
+        return dispatch_readout<LAT, S, T>(h, fin, flags, x, rho, u, ui, fpop, mp, err, corr, st);    \
+    }                                                                                                 \
+    template <>                                                                                       \
+    cudaError_t Launch<PREC, LAT>::init(const HostParams& h, const double* x, const double* n,             \
+                                   const double* fsrc, void* fprev, void* fcur, double* mp,           \
+                                   unsigned* err, cudaStream_t st)                                    \
+    {                                                                                                 \
+        return dispatch_init<LAT, S, T>(h, x, n, fsrc, fprev, fcur, mp, err, st);                          \
+    }                                                                                                 \
+    }

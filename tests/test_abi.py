@@ -1,0 +1,64 @@
+"""The C-ABI library on the CPU: it builds for sm_103a, loads without a GPU,
+exports every entry point include/evd.h declares, and validates arguments
+before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "evd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(evd_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(evd):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = evd.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(evd._SIGNATURES), "binding and header disagree"
+
+
+def test_version_and_required_bytes(evd):
+    assert evd.evd_version() == 1
+    sp = evd.SpeciesTable([2.0, 28.0, 44.0], np.full((3, 3), 0.05), 1.0, (0, -1e-6, 0))
+    g = evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP32, (64, 1024), evd.EVD_WALL_YM | evd.EVD_WALL_YP)
+    assert evd.evd_required_bytes(g, sp) == 64 * 1024 * 27 * 4
+    g3 = evd.make_grid(evd.EVD_D3Q19, evd.EVD_FP16_STORE, (5, 7, 3), 0)
+    # planes padded to 64 elements: 105 sites -> 128
+    assert evd.evd_required_bytes(g3, sp) == 128 * 57 * 2
+
+
+@pytest.mark.parametrize("bad", [
+    dict(lattice=7), dict(precision=9), dict(nz=2), dict(nx=0), dict(wall_mask=0b000100),
+    dict(M=[2.0, 1.0]), dict(M=[1.0, -2.0]), dict(tau1=0.5), dict(D=[[0, 0.05], [0.07, 0]]),
+    dict(D=[[0, -1.0], [-1.0, 0]]), dict(g=(0, 0, 1e-6)), dict(M=[1.0, 2.0, 3.0, 4.0]),
+    dict(wall_mask=0b010000)])
+def test_invalid_configurations_are_rejected_before_any_cuda_call(evd, bad):
+    M = bad.get("M", [1.0, 2.0])
+    ns = len(M)
+    D = bad.get("D", np.full((ns, ns), 0.05))
+    sp = evd.SpeciesTable(M, D, bad.get("tau1", 1.0), bad.get("g", (0, 0, 0)))
+    g = evd.evd_grid(bad.get("lattice", 0), bad.get("precision", 0), bad.get("nx", 4), 8,
+                     bad.get("nz", 1), bad.get("wall_mask", 0))
+    assert evd.evd_required_bytes(g, sp) == 0
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_create(g, sp)
+    assert ei.value.status == evd.EVD_ERR_ARG
+    assert evd.evd_last_error(None)
+
+
+def test_null_context_calls_fail_cleanly(evd):
+    L = evd.lib()
+    assert L.evd_step(None, 1) == evd.EVD_ERR_ARG
+    assert L.evd_check(None) == evd.EVD_ERR_ARG
+    assert L.evd_destroy(None) == evd.EVD_OK
+    assert L.evd_time(None) == -1
+    assert L.evd_launch_count(None) == -1
+    assert L.evd_set_mass_correction(None, 4) == evd.EVD_ERR_ARG

@@ -30,8 +30,12 @@ def test_generators_are_deterministic_and_valid():
 
 
 def test_paper_gases_fill_the_tube_halves():
-    wl = W.loschmidt_ternary_gravity(nx=4, ny=16)
-    # gas B (H2 rich) below, gas A (Ar rich) above, within the 1% noise
-    assert np.all(np.abs(wl.x[0, 0, :8] / 0.8 - 1) < 0.011)
-    assert np.all(np.abs(wl.x[2, 0, 8:] / 0.7 - 1) < 0.011)
+    wl = W.loschmidt_ternary_gravity(nx=4, ny=64)
+    # gas B (H2 rich) below, gas A (Ar rich) above, within the 1% noise, away
+    # from the smoothed interface between rows 31 and 32
+    assert np.all(np.abs(wl.x[0, 0, :16] / 0.8 - 1) < 0.011)
+    assert np.all(np.abs(wl.x[2, 0, 48:] / 0.7 - 1) < 0.011)
+    # the interface is monotone and centred
+    assert np.all(np.diff(wl.x[2, 0, 26:38, 0]) > 0)
+    assert abs(wl.x[2, 0, 31, 0] + wl.x[2, 0, 32, 0] - (0.7 + 0.001)) < 0.02
     assert np.all((wl.D[np.triu_indices(3, 1)] >= 0.02) & (wl.D[np.triu_indices(3, 1)] <= 0.1))
