@@ -191,6 +191,29 @@ evd_status evd_set_mass_correction(evd_ctx* ctx, int every);
 /* The FP64 target masses [n_species] (initial species masses).  Synchronises. */
 evd_status evd_get_target_mass(evd_ctx* ctx, double* m_host);
 
+/* Per-species total mass of a population array, without allocating.
+ * The paper has no counterpart; this is a service for callers that cannot
+ * call cudaMalloc: code whose device memory is owned by another allocator
+ * (a framework's caching pool or an application's fixed budget), and loops
+ * that must not pay the device-wide synchronisation cudaMalloc may cause.
+ * Such callers can compute the mass of a state they hold, for instance the
+ * output of evd_get_populations copied to their own device memory.
+ *   f_dev  device array [n_species][q][nsites] of doubles (dense, caller-owned)
+ *   n_species 1..3, q 9 (D2Q9) or 19 (D3Q19), nsites 1..2^40
+ *   m_dev  device array [n_species] receiving sum over directions and sites
+ * Asynchronous on cuda_stream (NULL = legacy default stream); sums in double
+ * in a fixed order.  Allocates nothing: the block partial sums live in a
+ * file-scope device array of 1024 x 3 doubles (24 KiB), present on every
+ * device that loads the library until the process exits.  Its address is
+ * looked up on the first call on each device (with that device current),
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (different streams, or several host
+ * threads) race and give wrong sums; serialise them.  Returns EVD_ERR_ARG
+ * for sizes beyond the limits above and EVD_ERR_CUDA if a launch fails;
+ * evd_last_error(NULL) then describes the problem. */
+evd_status evd_population_mass_noalloc(const double* f_dev, int n_species, int q,
+                                       long long nsites, double* m_dev, void* cuda_stream);
+
 /* Release the context and all memory the library allocated for it. */
 evd_status evd_destroy(evd_ctx* ctx);
 

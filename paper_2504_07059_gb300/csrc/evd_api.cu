@@ -25,6 +25,8 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+void evd::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct evd_ctx {
     HostParams hp;
     int lattice, precision, ns, Q, D;

@@ -4,7 +4,12 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 namespace evd {
+
+// Sets the message evd_last_error(NULL) returns on this thread.
+void set_thread_error(const std::string& msg);
 
 constexpr int MAXS = 3;
 

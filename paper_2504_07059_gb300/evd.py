@@ -76,6 +76,7 @@ _SIGNATURES = {
     "evd_launch_count": (ctypes.c_longlong, [_vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
+    "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
     "evd_destroy": (_st, [_vp]),
     "evd_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -249,6 +250,12 @@ def evd_set_mass_correction(ctx, every: int):
 
 def evd_get_target_mass(ctx, out):
     _check(lib().evd_get_target_mass(ctx, _ptr(out, writable=True)), ctx)
+
+
+def evd_population_mass_noalloc(f_dev, n_species: int, q: int, nsites: int, m_dev, stream=None):
+    """Species masses of a device population array; allocates nothing."""
+    _check(lib().evd_population_mass_noalloc(_ptr(f_dev), int(n_species), int(q), int(nsites),
+                                             _ptr(m_dev), _stream(stream)))
 
 
 def evd_destroy(ctx):
