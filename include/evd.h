@@ -180,6 +180,19 @@ evd_status evd_check(evd_ctx* ctx);
 /* Number of kernels this context has launched so far (launch accounting). */
 long long evd_launch_count(const evd_ctx* ctx);
 
+/* Step kernel.  EVD_KERNEL_TMA stages the interpolation stencil of every
+ * population plane in shared memory with TMA tile copies (D3Q19, FP32 or
+ * FP16 storage, walls in x and y, rows a multiple of 16 bytes); it is the
+ * default where it applies.  EVD_KERNEL_GENERAL handles every configuration
+ * (one thread per node, stencil read through the caches).  Both compute the
+ * same step.  EVD_KERNEL_AUTO picks the first that applies; asking for
+ * EVD_KERNEL_TMA where it does not apply is EVD_ERR_ARG. */
+#define EVD_KERNEL_AUTO 0
+#define EVD_KERNEL_GENERAL 1
+#define EVD_KERNEL_TMA 2
+evd_status evd_set_kernel(evd_ctx* ctx, int kernel);
+int evd_get_kernel(const evd_ctx* ctx);
+
 /* FP64 species-mass correction (not in the paper; a precision device for
  * FP32/FP16 storage).  Every `every` steps the step kernel also reduces the
  * per-species mass of f_t in double precision; the deficit from the initial

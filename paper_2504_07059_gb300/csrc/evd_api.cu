@@ -1,5 +1,7 @@
 // evd_api.cu -- the C ABI of libevd (declared in include/evd.h): context
 // management, validation, host-side constants, launches and readouts.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -50,6 +52,11 @@ struct evd_ctx {
     unsigned* err_flag;
     void* small;         // one allocation holding the five arrays above
     int mc_every;        // mass correction every k steps (0 = off)
+    bool tma_ok;         // the TMA-staged step can run this configuration
+    int kernel;          // EVD_KERNEL_GENERAL or EVD_KERNEL_TMA
+    int tma_blocks;      // grid of the TMA step
+    int last_parts;      // mass partials written by the last measuring launch
+    CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     int corr_pending;    // slot of a computed, not yet applied correction, or -1
     int corr_applied;    // slot the last step applied (the readout applies it too), or -1
     long long launches;  // kernels launched by this context
@@ -232,6 +239,14 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
     unsigned* e = c->err_flag;
     cudaStream_t st = c->stream;
     c->launches += 1;
+    if (c->kernel == EVD_KERNEL_TMA) {
+        const int in = (fin == c->buf[0]) ? 0 : 1;
+        c->last_parts = c->tma_blocks;
+        if (c->precision == EVD_FP32)
+            return evd::launch_step_tma<1>(h, c->tma[in], fin, fout, mp, e, flags, corr, st);
+        return evd::launch_step_tma<2>(h, c->tma[in], fin, fout, mp, e, flags, corr, st);
+    }
+    c->last_parts = c->nblocks;
     switch (c->precision * 2 + c->lattice) {
         case 0: return evd::Launch<0, 0>::step(h, fin, fout, mp, e, flags, corr, st);
         case 1: return evd::Launch<0, 1>::step(h, fin, fout, mp, e, flags, corr, st);
@@ -346,13 +361,63 @@ evd_status ensure_staging(evd_ctx* c, size_t bytes)
     return EVD_OK;
 }
 
-evd_status finish_mass(evd_ctx* c, double* out, const double* target = nullptr)
+evd_status finish_mass(evd_ctx* c, double* out, const double* target = nullptr, int parts = -1)
 {
     c->launches += 1;
-    evd_k_mass_finish<<<1, 1024, 0, c->stream>>>(c->mass_part, c->nblocks, c->ns, target,
+    evd_k_mass_finish<<<1, 1024, 0, c->stream>>>(c->mass_part, parts < 0 ? c->nblocks : parts, c->ns, target,
                                                  1.0 / (double)c->nsites, out);
     CK(c, cudaGetLastError());
     return EVD_OK;
+}
+
+// Tensor maps of the TMA-staged step: each population buffer seen as a 4-D
+// tensor (x, y, z, plane).  D3Q19 planes are stored [group][species][direction
+// in group] (groups of directions that move in the same dimensions); one map
+// per group, whose box is the tile plus a one-node halo in the in-plane
+// dimensions the group moves in (x halo widened to 16 bytes each side, the
+// TMA alignment), one z-plane, and all NS * group-size planes of the group.
+// Returns false when the configuration needs the general kernel: another
+// lattice or precision, periodic x or y, rows that are not a multiple of 16
+// bytes, or no driver entry point.
+bool tma_setup(evd_ctx* c)
+{
+    if (c->lattice != EVD_D3Q19 || c->precision == EVD_FP64) return false;
+    if (!c->hp.wall[0] || !c->hp.wall[1]) return false;
+    const size_t elem = c->elem;
+    if (((size_t)c->nx * elem) % 16 != 0) return false;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int TY = evd::TmaLaunch::TY, TX = evd::TmaLaunch::TX;
+    const int XP = (int)(16 / elem);
+    // storage groups: halo class (bit 0 x, bit 1 y) and number of directions
+    const int gcls[7] = {0, 0, 1, 1, 2, 2, 3};
+    const int gsize[7] = {1, 2, 2, 4, 2, 4, 4};
+    const cuuint64_t dims[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)(c->ns * 19)};
+    const cuuint64_t strides[3] = {(cuuint64_t)c->nx * elem, (cuuint64_t)c->nx * c->ny * elem,
+                                   (cuuint64_t)c->pstride * elem};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b)
+        for (int g = 0; g < 7; ++g) {
+            const int cls = gcls[g];
+            const cuuint32_t box[4] = {(cuuint32_t)((cls & 1) ? TX + 2 * XP : TX),
+                                       (cuuint32_t)((cls & 2) ? TY + 2 : TY), 1,
+                                       (cuuint32_t)(c->ns * gsize[g])};
+            const CUresult r = encode(&c->tma[b][g],
+                                      c->precision == EVD_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                      4, c->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    return true;
 }
 
 evd_status create_common(const evd_grid* grid, const evd_species* species, void* stream, void* pa,
@@ -396,7 +461,11 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
             }
         }
     }
-    const size_t part_bytes = ((size_t)c->nblocks * c->ns * sizeof(double) + 255) / 256 * 256;
+    c->tma_ok = tma_setup(c);
+    c->kernel = c->tma_ok ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL;
+    c->tma_blocks = c->tma_ok ? evd::TmaLaunch::grid(c->hp) : 0;
+    const int max_parts = c->nblocks > c->tma_blocks ? c->nblocks : c->tma_blocks;
+    const size_t part_bytes = ((size_t)max_parts * c->ns * sizeof(double) + 255) / 256 * 256;
     e = cudaMalloc(&c->small, part_bytes + 5 * 256);
     if (e != cudaSuccess) {
         if (c->own_bufs) { cudaFree(c->buf[0]); cudaFree(c->buf[1]); }
@@ -576,7 +645,7 @@ evd_status evd_step(evd_ctx* c, long long nsteps)
         c->corr_pending = -1;
         if (measure) {
             const int slot = (apply == 0) ? 1 : 0;
-            evd_status s = finish_mass(c, c->corr[slot], c->m_target);
+            evd_status s = finish_mass(c, c->corr[slot], c->m_target, c->last_parts);
             if (s != EVD_OK) return s;
             c->corr_pending = slot;
         }
@@ -666,13 +735,28 @@ evd_status evd_check(evd_ctx* c)
     if (flag) {
         std::string m = "unstable state:";
         if (flag & 1u) m += " non-positive or NaN species density;";
-        if (flag & 2u) m += " cross relaxation time tau_ij <= 1/2 or NaN;";
+        if (flag & 2u) m += " non-positive or non-finite cross relaxation time;";
+        if (flag & 4u) return fail(c, EVD_ERR_TIMEOUT, "a device-side wait for a tile copy gave up");
         return fail(c, EVD_ERR_UNSTABLE, m);
     }
     return EVD_OK;
 }
 
 long long evd_launch_count(const evd_ctx* c) { return c ? c->launches : -1; }
+
+evd_status evd_set_kernel(evd_ctx* c, int kernel)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (kernel == EVD_KERNEL_AUTO) kernel = c->tma_ok ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL;
+    if (kernel == EVD_KERNEL_TMA && !c->tma_ok)
+        return fail(c, EVD_ERR_ARG, "the TMA-staged step needs D3Q19, FP32 or FP16 storage, walls in x and y "
+                                    "and rows of a multiple of 16 bytes");
+    if (kernel != EVD_KERNEL_GENERAL && kernel != EVD_KERNEL_TMA) return fail(c, EVD_ERR_ARG, "unknown kernel");
+    c->kernel = kernel;
+    return EVD_OK;
+}
+
+int evd_get_kernel(const evd_ctx* c) { return c ? c->kernel : 0; }
 
 evd_status evd_set_mass_correction(evd_ctx* c, int every)
 {

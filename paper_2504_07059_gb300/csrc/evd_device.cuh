@@ -9,9 +9,9 @@
 // wall-adjacent nodes) into f_t, computes the moments, the cross relaxation
 // times and the collision of Eq. (LBE_forcing), and writes f*_t.
 //
-// Layout in HBM: structure of arrays, one plane per (species, direction),
-// plane p = i*Q + a at element offset p * pstride, x fastest inside a plane,
-// pstride rounded up to 64 elements so every plane starts 128-byte aligned.
+// Layout in HBM: structure of arrays, one plane per (species, direction) at
+// element offset plane_of(i, a) * pstride, x fastest inside a plane, pstride
+// rounded up to 64 elements so every plane starts 128-byte aligned.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -76,6 +76,37 @@ template <int LAT>
 __host__ __device__ constexpr int wclass(int a)
 {
     return (ev<LAT>(a, 0) != 0) + (ev<LAT>(a, 1) != 0) + (ev<LAT>(a, 2) != 0);
+}
+
+// Storage order of the population planes.  D2Q9: plane = i*9 + a.  D3Q19:
+// directions are grouped by the dimensions they move in, G0 {0}, G1 {5,6},
+// G2 {1,2}, G3 {11..14}, G4 {3,4}, G5 {15..18}, G6 {7..10}, and stored
+// [group][species][direction in group], so that the planes one tile copy of
+// the TMA-staged step needs (same halo shape, all species) are contiguous.
+template <int LAT>
+__host__ __device__ constexpr int grp(int a)
+{
+    return LAT == 0 ? 0
+                    : (a == 0 ? 0 : (a == 5 || a == 6) ? 1 : (a == 1 || a == 2) ? 2 : (a >= 11 && a <= 14) ? 3
+                       : (a == 3 || a == 4) ? 4 : (a >= 15) ? 5 : 6);
+}
+__host__ __device__ constexpr int grp_start(int g)
+{
+    return g == 0 ? 0 : g == 1 ? 1 : g == 2 ? 3 : g == 3 ? 5 : g == 4 ? 9 : g == 5 ? 11 : 15;
+}
+__host__ __device__ constexpr int grp_size(int g) { return g == 0 ? 1 : (g == 1 || g == 2 || g == 4) ? 2 : 4; }
+template <int LAT>
+__host__ __device__ constexpr int grp_pos(int a)
+{
+    return LAT == 0 ? a
+                    : (a == 0 ? 0 : (a == 5 || a == 6) ? a - 5 : (a == 1 || a == 2) ? a - 1
+                       : (a >= 11 && a <= 14) ? a - 11 : (a == 3 || a == 4) ? a - 3 : (a >= 15) ? a - 15 : a - 7);
+}
+template <int LAT, int NS>
+__host__ __device__ constexpr int plane_of(int i, int a)
+{
+    return LAT == 0 ? i * 9 + a
+                    : NS * grp_start(grp<LAT>(a)) + i * grp_size(grp<LAT>(a)) + grp_pos<LAT>(a);
 }
 
 // --------------------------------------------------------------- parameters
@@ -184,12 +215,12 @@ __host__ __device__ constexpr int widx(int o, int e) { return o == -e ? 0 : (o =
 // Interior node: f_a(O) = sum over the 1/3/9 stencil nodes O + o of
 // W(o) f*_a(O + o), the tensor product of 1-D weights along the (one or two)
 // dimensions direction a moves in.
-template <int LAT, int I, int A, typename S, typename T>
+template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __restrict__ fin, int node,
                                              const Nbr& nb)
 {
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
-    const S* plane = fin + (long long)(I * Lat<LAT>::Q + A) * p.pstride + node;
+    const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
     T acc;
     if constexpr (ex == 0 && ey == 0 && ez == 0) {
         acc = (T)Codec<S>::ld(plane);
@@ -280,14 +311,13 @@ __device__ __forceinline__ T lumped(const Params<T>& p, int I, const Nbr& nb, bo
 
 // Wall-adjacent node: only fluid stencil nodes contribute, plus the lumped
 // weight of O's own populations in directions a and its opposite.
-template <int LAT, int I, int A, typename S, typename T>
+template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict__ fin, int node,
                                          const Nbr& nb)
 {
-    constexpr int Q = Lat<LAT>::Q;
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
     constexpr int AB = opp<LAT>(A);
-    const S* plane = fin + (long long)(I * Q + A) * p.pstride + node;
+    const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
     const T ref = Codec<S>::DEV ? p.ref[I][wclass<LAT>(A)] : (T)0;
     T acc = (T)0;
 #pragma unroll
@@ -309,7 +339,8 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
         const T ls = lumped<LAT, A>(p, I, nb, true);
         const T lo = lumped<LAT, AB>(p, I, nb, false);
         if (ls != (T)0) acc += ls * ((T)Codec<S>::ld(plane) + ref);
-        if (lo != (T)0) acc += lo * ((T)Codec<S>::ld(fin + (long long)(I * Q + AB) * p.pstride + node) + ref);
+        if (lo != (T)0)
+            acc += lo * ((T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node) + ref);
     }
     return acc;
 }
@@ -324,7 +355,7 @@ __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restri
             constexpr int I = decltype(ic)::value;
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_interior<LAT, I, A>(p, fin, node, nb);
+                f[I][A] = gather_interior<LAT, NS, I, A>(p, fin, node, nb);
             });
         });
     } else {
@@ -332,7 +363,7 @@ __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restri
             constexpr int I = decltype(ic)::value;
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_wall<LAT, I, A>(p, fin, node, nb);
+                f[I][A] = gather_wall<LAT, NS, I, A>(p, fin, node, nb);
             });
         });
     }
@@ -347,7 +378,7 @@ __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict
         constexpr int I = decltype(ic)::value;
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
-            T v = (T)Codec<S>::ld(fin + (long long)(I * Q + A) * p.pstride + node);
+            T v = (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
             if constexpr (Codec<S>::DEV) v += p.ref[I][wclass<LAT>(A)];
             f[I][A] = v;
         });
@@ -365,7 +396,7 @@ __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fo
             constexpr int A = decltype(ac)::value;
             T v = f[I][A];
             if constexpr (Codec<S>::DEV) v -= p.ref[I][wclass<LAT>(A)];
-            Codec<S>::st(fout + (long long)(I * Q + A) * p.pstride + node, v);
+            Codec<S>::st(fout + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node, v);
         });
     });
 }

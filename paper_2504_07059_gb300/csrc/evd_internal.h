@@ -46,4 +46,21 @@ struct Launch {
 
 inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + block - 1) / block; }
 
+// The D3Q19 step with TMA-staged tiles (float and half storage only).
+// maps points to the seven tensor maps (CUtensorMap, 128 bytes each) of the
+// input buffer, one per storage group of directions.
+struct TmaLaunch {
+    static constexpr int TX = 32, TY = 4, SLOTS = 4, NGROUPS = 7;
+    static int zchunk(const HostParams& h) { return h.nz < 32 ? h.nz : 32; }
+    static int grid(const HostParams& h)
+    {
+        const int ntx = (h.nx + TX - 1) / TX, nty = (h.ny + TY - 1) / TY, zc = zchunk(h);
+        return ntx * nty * ((h.nz + zc - 1) / zc);
+    }
+};
+
+template <int PREC>
+cudaError_t launch_step_tma(const HostParams& h, const void* maps, const void* fin, void* fout,
+                            double* mass_part, unsigned* err, int flags, const double* corr, cudaStream_t st);
+
 }  // namespace evd

@@ -76,3 +76,14 @@ cudaError_t dispatch_init(const HostParams& h, const double* x, const double* n,
         return dispatch_init<LAT, S, T>(h, x, n, fsrc, fprev, fcur, mp, err, st);                          \
     }                                                                                                 \
     }
+
+#define EVD_DEFINE_TMA_LAUNCHER(PREC, S)                                                              \
+    namespace evd {                                                                                   \
+    template <>                                                                                       \
+    cudaError_t launch_step_tma<PREC>(const HostParams& h, const void* maps, const void* fin,         \
+                                      void* fout, double* mp, unsigned* err, int flags,               \
+                                      const double* corr, cudaStream_t st)                            \
+    {                                                                                                 \
+        return dispatch_step_tma<S>(h, maps, fin, fout, mp, err, flags, corr, st);                    \
+    }                                                                                                 \
+    }

@@ -1,0 +1,502 @@
+// evd_tma.cuh -- the D3Q19 step with TMA-staged tiles (float / half storage).
+//
+// Work decomposition.  A CTA owns a column of TX x TY nodes in (x, y) and a
+// chunk of z.  It has one compute thread per (node, species) -- warp w <
+// TY*NS holds the 32 x-nodes of row w % TY for species w / TY -- and one
+// producer warp.  The CTA marches up its z-chunk.  For every z-plane the
+// producer brings, with one TMA tile copy (cp.async.bulk.tensor) per storage
+// group, the slabs of every (species, direction) plane into a ring of SLOTS
+// shared-memory stages: the tile plus a one-node halo along the in-plane
+// dimensions the group's directions move in.  Each stage has a "full"
+// mbarrier (completed by the copies' transaction bytes) and an "empty"
+// mbarrier (one arrival per compute warp once it has read the stage), so the
+// producer runs up to SLOTS stages ahead and the compute warps never wait for
+// copies to be issued.
+//
+// Each slab is read once: its in-plane interpolation R (1, 3 or 3x3 points of
+// Eq. Second_order_spatial_interpolation) is formed in registers, then
+//   * directions without a z component keep R as the value of the node at
+//     that z (delayed one iteration, so the slab need not stay resident);
+//   * directions with a z component add w(oz) R to the running sums of the
+//     nodes at z+1, z and z-1 (the z-part of the tensor-product weights),
+//     and the node at z-1 is complete.
+// So iteration k of the march finishes the node at z = k - 1.  The species of
+// a node then exchange rho_i and u_i^eq through shared memory (one barrier of
+// the compute warps per iteration) for the cross collision, and each thread
+// collides and stores its own 19 populations.
+//
+// Walls: a thread's (x, y) column is fixed for the whole march, so solid
+// in-plane stencil nodes are removed once, by zeroing their weights; a z-slab
+// beyond a z wall contributes nothing.  Wall-adjacent nodes add the App. A
+// lumped terms, for which they read their own two populations from global
+// memory.  Periodic z is a wrapped slab coordinate; x and y must be walled
+// (other geometries use the general kernel).
+#pragma once
+
+#include <cuda.h>
+
+#include "evd_device.cuh"
+
+namespace evd {
+
+constexpr int TTX = 32;
+constexpr int NGRP = 7;
+constexpr unsigned ERR_TIMEOUT = 4u;
+
+template <typename S> struct TmaPad;
+template <> struct TmaPad<float> { static constexpr int XP = 4; };   // 16 bytes
+template <> struct TmaPad<__half> { static constexpr int XP = 8; };  // 16 bytes
+
+// halo class of a storage group: bit 0 moves in x, bit 1 moves in y
+__host__ __device__ constexpr int grp_cls(int g) { return g == 2 || g == 3 ? 1 : g == 4 || g == 5 ? 2 : g == 6 ? 3 : 0; }
+__host__ __device__ constexpr bool grp_moves_z(int g) { return g == 1 || g == 3 || g == 5; }
+
+template <int NS, typename S, int TY, int SLOTS>
+struct TmaLayout {
+    static constexpr int XP = TmaPad<S>::XP;
+    static __host__ __device__ constexpr int bw(int cls) { return (cls & 1) ? TTX + 2 * XP : TTX; }
+    static __host__ __device__ constexpr int bh(int cls) { return (cls & 2) ? TY + 2 : TY; }
+    static __host__ __device__ constexpr int plane_elems(int g) { return bw(grp_cls(g)) * bh(grp_cls(g)); }
+    static __host__ __device__ constexpr int box_bytes(int g)
+    {
+        return plane_elems(g) * NS * grp_size(g) * (int)sizeof(S);
+    }
+    static __host__ __device__ constexpr int group_offset(int g)
+    {
+        int o = 0;
+        for (int q = 0; q < g; ++q) o += (box_bytes(q) + 127) / 128 * 128;
+        return o;
+    }
+    static constexpr int slot_bytes = group_offset(NGRP);
+    static __host__ __device__ constexpr int stage_bytes(bool zonly)
+    {
+        int s = 0;
+        for (int g = 0; g < NGRP; ++g)
+            if (!zonly || grp_moves_z(g)) s += box_bytes(g);
+        return s;
+    }
+    static constexpr int ring_bytes = SLOTS * slot_bytes;
+    static constexpr int exch_bytes = 2 * NS * TY * TTX * 16;   // two float4 buffers
+    static constexpr int msum_offset = ring_bytes + exch_bytes;
+    static constexpr int bar_offset = msum_offset + NS * TY * 8 + 8;
+    static constexpr int total_bytes = bar_offset + 2 * SLOTS * 8 + 128;   // + alignment slack
+    static constexpr int consumers = TTX * TY * NS;
+    static constexpr int threads = consumers + 32;
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after 2^22 polls (far longer than any copy takes).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Barrier 1 among the compute warps only, returning the OR of v over them.
+__device__ __forceinline__ bool consumers_sync_or(bool v, int nthreads)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+struct TmaMaps {
+    CUtensorMap m[NGRP];   // one per storage group of the input buffer
+};
+
+// Which z-planes a stage loads: all groups for z in [zb, ze), only the
+// z-moving groups for the halo planes zb-1 and ze.
+__device__ __forceinline__ bool stage_is_halo(int k, int zb, int ze) { return k < zb || k >= ze; }
+
+// masked 1-D weights of one in-plane dimension for a direction component e
+// (+1 -> index 0, -1 -> index 1): solid stencil nodes get weight zero
+struct MaskedW {
+    float w[2][3];
+    float sum[2];
+};
+
+__device__ __forceinline__ MaskedW masked_weights(const float (&w)[3], bool lo, bool hi)
+{
+    MaskedW m;
+#pragma unroll
+    for (int ei = 0; ei < 2; ++ei) {
+        const int e = ei == 0 ? 1 : -1;
+        float s = 0.0f;
+#pragma unroll
+        for (int o = -1; o <= 1; ++o) {
+            const bool solid = (o == -1 && lo) || (o == 1 && hi);
+            const float v = solid ? 0.0f : w[o == -e ? 0 : (o == 0 ? 1 : 2)];
+            m.w[ei][o + 1] = v;
+            s += v;
+        }
+        m.sum[ei] = s;
+    }
+    return m;
+}
+
+// In-plane interpolation of direction A (decoded: includes the deviation
+// reference scaled by the weight the fluid stencil nodes carry).
+template <int A, int NS, typename S, int TY, int SLOTS>
+__device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int tx, int ty, const MaskedW& mx,
+                                         const MaskedW& my, float ref)
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
+    constexpr int g = grp<1>(A);
+    constexpr int cls = grp_cls(g);
+    constexpr int W = G::bw(cls);
+    constexpr int xi = ex > 0 ? 0 : 1, yi = ey > 0 ? 0 : 1;
+    const S* s = reinterpret_cast<const S*>(slot + G::group_offset(g)) +
+                 (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
+    const int cx = tx + ((cls & 1) ? G::XP : 0);
+    const int cy = ty + ((cls & 2) ? 1 : 0);
+    auto ld = [&](int yy, int xx) -> float { return (float)s[yy * W + xx]; };
+    if constexpr (cls == 0) {
+        return ld(cy, cx) + ref;
+    } else if constexpr (cls == 1) {
+        return mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1) +
+               ref * mx.sum[xi];
+    } else if constexpr (cls == 2) {
+        return my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx) +
+               ref * my.sum[yi];
+    } else {
+        float acc = 0.0f;
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy) {
+            const float row = mx.w[xi][0] * ld(cy + oy, cx - 1) + mx.w[xi][1] * ld(cy + oy, cx) +
+                              mx.w[xi][2] * ld(cy + oy, cx + 1);
+            acc += my.w[yi][oy + 1] * row;
+        }
+        return acc + ref * mx.sum[xi] * my.sum[yi];
+    }
+}
+
+template <int NS, typename S, int TY, int SLOTS>
+__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, 1)
+k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
+           S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
+           const double* __restrict__ corr, int ntx, int nty, int zchunk)
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    constexpr int Q = 19;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    float4* exch = reinterpret_cast<float4*>(smem + G::ring_bytes);
+    double* msum = reinterpret_cast<double*>(smem + G::msum_offset);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + G::bar_offset);
+    const unsigned ring = smem_u32(smem);
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[SLOTS + s]); };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x % (ntx * nty);
+    const int chunk = blockIdx.x / (ntx * nty);
+    const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
+    const int zb = chunk * zchunk;
+    const int ze = min(zb + zchunk, p.nz);
+    const int zwall = p.wall[2];
+    const int kfirst = zb - 1;
+    const int nstage = ze - zb + 2;   // stages k = zb-1 .. ze
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SLOTS; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), TY * NS);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TY * NS) {
+        // ------------------------------------------------------ producer
+        const int g = lane;   // lanes 0..6 each own one storage group
+        const int cls = grp_cls(g < NGRP ? g : 0);
+        const int cx = (cls & 1) ? x0 - G::XP : x0;
+        const int cy = (cls & 2) ? y0 - 1 : y0;
+        const int c3 = NS * grp_start(g < NGRP ? g : 0);
+        const unsigned goff = (unsigned)G::group_offset(g < NGRP ? g : 0);
+        const bool moves_z = g < NGRP && grp_moves_z(g);
+        bool ok = true;
+        for (int idx = 0; idx < nstage && ok; ++idx) {
+            const int slot = idx % SLOTS;
+            if (idx >= SLOTS) ok = mbar_wait_bounded(empty(slot), (unsigned)(((idx / SLOTS) - 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const int k = kfirst + idx;
+            const bool halo = stage_is_halo(k, zb, ze);
+            const int zc = zwall ? k : (k % p.nz + p.nz) % p.nz;   // walled: out of range -> zero fill
+            if (lane == 0) mbar_arrive_expect_tx(full(slot), (unsigned)G::stage_bytes(halo));
+            __syncwarp();
+            if (g < NGRP && (!halo || moves_z))
+                tma_load_4d(ring + (unsigned)(slot * G::slot_bytes) + goff, &maps.m[g], cx, cy, zc, c3, full(slot));
+        }
+        if (!ok && lane == 0) atomicOr(err_flag, ERR_TIMEOUT);
+        return;
+    }
+
+    // ------------------------------------------------------------ consumers
+    const int ty = warp % TY, sp = warp / TY;
+    const int tx = lane;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < p.nx && y < p.ny;
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w[a] = p.w1[sp][a];
+    const float ref_c[3] = {p.ref[sp][0], p.ref[sp][1], p.ref[sp][2]};
+    const float csp = p.c[sp], inv_cs2 = p.inv_cs2[sp], c_inv_cs2 = p.c_inv_cs2[sp];
+    const float tau_inv = p.tau_inv[sp], omt = p.omt[sp], sfac = p.sfac[sp];
+    const bool xlo = p.wall[0] && x == 0, xhi = p.wall[0] && x == p.nx - 1;
+    const bool ylo = p.wall[1] && y == 0, yhi = p.wall[1] && y == p.ny - 1;
+    const bool col_wall = xlo || xhi || ylo || yhi;
+    const MaskedW mx = masked_weights(w, xlo, xhi), my = masked_weights(w, ylo, yhi);
+    const int nxy = p.nx * p.ny;
+
+    // running sums: z-moving directions (A: node at z = k-1, B: node at k),
+    // in-plane directions (N: value at z = k-1)
+    float accA[Q], accB[Q], accN[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) accA[a] = accB[a] = accN[a] = 0.0f;
+    double mass_acc = 0.0;
+    unsigned err = 0;
+    bool failed = false;
+
+    for (int idx = 0; idx < nstage; ++idx) {
+        const int k = kfirst + idx;
+        const int slot = idx % SLOTS;
+        const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
+        const unsigned char* base = smem + slot * G::slot_bytes;
+        const bool halo = stage_is_halo(k, zb, ze);
+        const bool solid_slab = zwall && (k < 0 || k >= p.nz);
+        const int zo = k - 1;                   // node finished this iteration
+        const bool emit = zo >= zb && zo < ze;  // the same for every thread of the CTA
+        float f[Q];
+        if (ok) {
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                constexpr int ez = ev<1>(A, 2);
+                const float ref = ref_c[wclass<1>(A)];
+                if constexpr (ez == 0) {
+                    f[A] = accN[A];
+                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref);
+                } else {
+                    const float R = solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref);
+                    // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
+                    f[A] = accA[A] + w[widx(1, ez)] * R;
+                    accA[A] = accB[A] + w[widx(0, ez)] * R;
+                    accB[A] = w[widx(-1, ez)] * R;
+                }
+            });
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(slot));   // this warp is done with the stage
+
+        // ---- node (x, y, zo): wall terms, correction, moments
+        float rho = 1.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
+        const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
+        const int node = x + p.nx * y + nxy * zo;
+        if (ok && emit) {
+            if (active && (col_wall || zlo || zhi)) {
+                Nbr nb;
+                nb.lo[0] = xlo; nb.hi[0] = xhi; nb.lo[1] = ylo; nb.hi[1] = yhi; nb.lo[2] = zlo; nb.hi[2] = zhi;
+                static_for<1, Q>([&](auto ac) {
+                    constexpr int A = decltype(ac)::value;
+                    constexpr int AB = opp<1>(A);
+                    const float ref = ref_c[wclass<1>(A)];
+                    const float ls = lumped<1, A>(p, sp, nb, true);
+                    const float lo = lumped<1, AB>(p, sp, nb, false);
+                    const long long pa = (long long)plane_of<1, NS>(sp, A) * p.pstride + node;
+                    const long long pb = (long long)plane_of<1, NS>(sp, AB) * p.pstride + node;
+                    if (ls != 0.0f) f[A] += ls * ((float)fin[pa] + ref);
+                    if (lo != 0.0f) f[A] += lo * ((float)fin[pb] + ref);
+                });
+            }
+            if (corr) {
+                const float ci = (float)__ldg(corr + sp);
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int A = decltype(ac)::value;
+                    f[A] = fmaf(p.wl[wclass<1>(A)], ci, f[A]);
+                });
+            }
+            float r = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                r += f[A];
+                if constexpr (ev<1>(A, 0) == 1) j[0] += f[A];
+                if constexpr (ev<1>(A, 0) == -1) j[0] -= f[A];
+                if constexpr (ev<1>(A, 1) == 1) j[1] += f[A];
+                if constexpr (ev<1>(A, 1) == -1) j[1] -= f[A];
+                if constexpr (ev<1>(A, 2) == 1) j[2] += f[A];
+                if constexpr (ev<1>(A, 2) == -1) j[2] -= f[A];
+            });
+            if (active && !(r > 0.0f)) err |= ERR_RHO;
+            rho = r;
+            const float rinv = 1.0f / r;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ueq[d] = csp * j[d] * rinv + 0.5f * p.g[d];
+            exch[((idx & 1) * NS * TY + sp * TY + ty) * TTX + tx] = make_float4(rho, ueq[0], ueq[1], ueq[2]);
+        }
+        // one barrier of the compute warps per iteration: the exchange, and
+        // agreement on a failed wait
+        failed = consumers_sync_or(!ok, G::consumers);
+        if (failed) break;
+        if (!emit) continue;
+
+        // ---- species coupling (every thread of the node recomputes it)
+        float r[NS], ue[NS][3];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const float4 v = exch[((idx & 1) * NS * TY + i * TY + ty) * TTX + tx];
+            r[i] = v.x; ue[i][0] = v.y; ue[i][1] = v.z; ue[i][2] = v.w;
+        }
+        float rho_m = 0.0f, n = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) { rho_m += r[i]; n += r[i] * p.Minv[i]; }
+        const float rinv_m = 1.0f / rho_m;
+        float u[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc += r[i] * ue[i][d];
+            u[d] = acc * rinv_m;
+        }
+        float X[MAXS][MAXS] = {};
+        if constexpr (NS == 2) {
+            const float A12 = (r[0] + r[1]) * p.iD[0][1] + n * p.MM[0][1];
+            X[0][1] = X[1][0] = 2.0f * rho_m * p.iD[0][1] / A12;
+        } else if constexpr (NS == 3) {
+            const float A12 = (r[0] + r[1]) * p.iD[0][1] + n * p.MM[0][1];
+            const float A13 = (r[0] + r[2]) * p.iD[0][2] + n * p.MM[0][2];
+            const float A23 = (r[1] + r[2]) * p.iD[1][2] + n * p.MM[1][2];
+            const float B12 = 2.0f * rho_m * p.iD[0][1];
+            const float B13 = 2.0f * rho_m * p.iD[0][2];
+            const float B23 = 2.0f * rho_m * p.iD[1][2];
+            const float rA13 = 1.0f / A13;
+            const float X23 = (B23 - r[0] * B13 * rA13 * p.iD[1][2]) /
+                              (A23 - r[0] * r[1] * rA13 * p.iD[0][2] * p.iD[1][2]);
+            X[0][1] = X[1][0] = (B12 - r[2] * X23 * p.iD[0][1]) / A12;
+            X[0][2] = X[2][0] = (B13 - r[1] * X23 * p.iD[0][2]) * rA13;
+            X[1][2] = X[2][1] = X23;
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+#pragma unroll
+            for (int jj = i + 1; jj < NS; ++jj)
+                if (active && (!(X[i][jj] > 0.0f) || !isfinite(X[i][jj]))) err |= ERR_TAU;
+        float V[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int jj = 0; jj < NS; ++jj) {
+                float xs = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) xs = (i == sp) ? X[i][jj] : xs;
+                if (jj != sp) acc += r[jj] * xs * (ueq[d] - ue[jj][d]);
+            }
+            V[d] = acc * rinv_m;
+        }
+
+        // ---- collision of this species (same algebra as the general kernel)
+        const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const float ug = u[0] * p.g[0] + u[1] * p.g[1] + u[2] * p.g[2];
+        float av[3], ua = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            av[d] = (ueq[d] - u[d]) * tau_inv - V[d];
+            ua += u[d] * av[d];
+        }
+        const float Bc = tau_inv - inv_cs2 * ua;
+        const float U2 = 1.0f - 0.5f * inv_cs2 * usq;
+        const float wr[3] = {p.wl[0] * rho, p.wl[1] * rho, p.wl[2] * rho};
+        const float sr = rho * inv_cs2 * sfac;
+        if (active) mass_acc += (double)rho;
+        static_for<0, Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            constexpr int C = wclass<1>(A);
+            const float eu = edot<1, A>(u);
+            const float eg = edot<1, A>(p.g);
+            const float ea = edot<1, A>(av);
+            const float t1 = c_inv_cs2 * eu;
+            const float feq = wr[C] * fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
+            const float B = fmaf(c_inv_cs2, ea, Bc);
+            const float S_ = p.wl[C] * sr * fmaf(csp * eg, 1.0f + t1, -ug);
+            const float fs = fmaf(omt, f[A], fmaf(feq, B, S_));
+            if (active)
+                Codec<S>::st(fout + (long long)plane_of<1, NS>(sp, A) * p.pstride + node, fs - ref_c[C]);
+        });
+    }
+
+    if (failed) {
+        // never expected: report and leave (the producer gives up as well)
+        if (threadIdx.x == 0) atomicOr(err_flag, ERR_TIMEOUT);
+        return;
+    }
+    if (err) atomicOr(err_flag, err);
+    if (flags & F_MASS) {
+        // per-species block partial over the TY warps of a species, fixed order
+        double v = mass_acc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) msum[sp * TY + ty] = v;
+        (void)consumers_sync_or(false, G::consumers);
+        if (threadIdx.x < NS) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < TY; ++q) t += msum[threadIdx.x * TY + q];
+            mass_part[(long long)blockIdx.x * NS + threadIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace evd

@@ -22,6 +22,7 @@ EVD_D2Q9, EVD_D3Q19 = 0, 1
 EVD_FP64, EVD_FP32, EVD_FP16_STORE = 0, 1, 2
 EVD_WALL_XM, EVD_WALL_XP, EVD_WALL_YM, EVD_WALL_YP, EVD_WALL_ZM, EVD_WALL_ZP = (1, 2, 4, 8, 16, 32)
 EVD_MAX_SPECIES = 3
+EVD_KERNEL_AUTO, EVD_KERNEL_GENERAL, EVD_KERNEL_TMA = 0, 1, 2
 
 STATUS_NAMES = {0: "EVD_OK", 1: "EVD_ERR_ARG", 2: "EVD_ERR_CUDA", 3: "EVD_ERR_UNSTABLE",
                 4: "EVD_ERR_TIMEOUT", 5: "EVD_ERR_STATE"}
@@ -74,6 +75,8 @@ _SIGNATURES = {
     "evd_time": (ctypes.c_longlong, [_vp]),
     "evd_check": (_st, [_vp]),
     "evd_launch_count": (ctypes.c_longlong, [_vp]),
+    "evd_set_kernel": (_st, [_vp, ctypes.c_int]),
+    "evd_get_kernel": (ctypes.c_int, [_vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
@@ -242,6 +245,14 @@ def evd_check(ctx):
 
 def evd_launch_count(ctx) -> int:
     return lib().evd_launch_count(ctx)
+
+
+def evd_set_kernel(ctx, kernel: int):
+    _check(lib().evd_set_kernel(ctx, int(kernel)), ctx)
+
+
+def evd_get_kernel(ctx) -> int:
+    return lib().evd_get_kernel(ctx)
 
 
 def evd_set_mass_correction(ctx, every: int):
