@@ -57,6 +57,7 @@ struct evd_ctx {
     int tma_blocks;      // grid of the TMA step
     int last_parts;      // mass partials written by the last measuring launch
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
+    float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
     int corr_pending;    // slot of a computed, not yet applied correction, or -1
     int corr_applied;    // slot the last step applied (the readout applies it too), or -1
     long long launches;  // kernels launched by this context
@@ -243,8 +244,8 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
         const int in = (fin == c->buf[0]) ? 0 : 1;
         c->last_parts = c->tma_blocks;
         if (c->precision == EVD_FP32)
-            return evd::launch_step_tma<1>(h, c->tma[in], fin, fout, mp, e, flags, corr, st);
-        return evd::launch_step_tma<2>(h, c->tma[in], fin, fout, mp, e, flags, corr, st);
+            return evd::launch_step_tma<1>(h, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
+        return evd::launch_step_tma<2>(h, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
     }
     c->last_parts = c->nblocks;
     switch (c->precision * 2 + c->lattice) {
@@ -379,10 +380,78 @@ evd_status finish_mass(evd_ctx* c, double* out, const double* target = nullptr, 
 // Returns false when the configuration needs the general kernel: another
 // lattice or precision, periodic x or y, rows that are not a multiple of 16
 // bytes, or no driver entry point.
+// D3Q19 unit vectors in the library's direction order (include/evd.h).
+const int kE19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                         {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                         {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                         {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+int opp19(int a)
+{
+    for (int b = 0; b < 19; ++b)
+        if (kE19[b][0] == -kE19[a][0] && kE19[b][1] == -kE19[a][1] && kE19[b][2] == -kE19[a][2]) return b;
+    return 0;
+}
+
+// App. A lumped weight of direction b leaving a node of the given wall class
+// (lo/hi per dimension): the push weight bound for solid nodes that stays at
+// the node, in b itself (into_self) or in its opposite.  The rule: stays in
+// b unless b heads into the crossed wall(s), e_b . d_s > 0.
+double lump_weight(const HostParams& h, int i, int b, const bool lo[3], const bool hi[3], bool into_self)
+{
+    double acc = 0.0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int d[3] = {dx, dy, dz};
+                bool skip = false, crossed = false;
+                int dot = 0;
+                double w = 1.0;
+                for (int k = 0; k < 3; ++k) {
+                    const int e = kE19[b][k];
+                    if (e == 0) {
+                        if (d[k] != 0) skip = true;
+                        continue;
+                    }
+                    w *= h.w1[i][d[k] == e ? 0 : (d[k] == 0 ? 1 : 2)];
+                    const bool cr = (d[k] == 1 && hi[k]) || (d[k] == -1 && lo[k]);
+                    crossed |= cr;
+                    if (cr) dot += e * d[k];
+                }
+                if (skip || !crossed) continue;
+                if ((dot > 0) != into_self) acc += w;
+            }
+    return acc;
+}
+
+// Table [27 wall classes][ns][19] of (L_self, L_opp) floats for the TMA step.
+bool build_lumps(evd_ctx* c)
+{
+    const int n = 27 * c->ns * 19 * 2;
+    float* host = new float[n];
+    for (int cls = 0; cls < 27; ++cls) {
+        const int cc[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+        bool lo[3], hi[3];
+        for (int k = 0; k < 3; ++k) { lo[k] = cc[k] == 1; hi[k] = cc[k] == 2; }
+        for (int i = 0; i < c->ns; ++i)
+            for (int a = 0; a < 19; ++a) {
+                float* t = host + ((cls * c->ns + i) * 19 + a) * 2;
+                t[0] = a ? (float)lump_weight(c->hp, i, a, lo, hi, true) : 0.0f;
+                t[1] = a ? (float)lump_weight(c->hp, i, opp19(a), lo, hi, false) : 0.0f;
+            }
+    }
+    bool ok = cudaMalloc((void**)&c->lumps, n * sizeof(float)) == cudaSuccess &&
+              cudaMemcpy(c->lumps, host, n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    delete[] host;
+    return ok;
+}
+
 bool tma_setup(evd_ctx* c)
 {
     if (c->lattice != EVD_D3Q19 || c->precision == EVD_FP64) return false;
     if (!c->hp.wall[0] || !c->hp.wall[1]) return false;
+    if (c->nx < 2 || c->ny < 2 || (c->hp.wall[2] && c->nz < 2)) return false;
+    if ((long long)c->ns * 19 * c->pstride >= (1LL << 31)) return false;
     const size_t elem = c->elem;
     if (((size_t)c->nx * elem) % 16 != 0) return false;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -417,7 +486,7 @@ bool tma_setup(evd_ctx* c)
                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return false;
         }
-    return true;
+    return build_lumps(c);
 }
 
 evd_status create_common(const evd_grid* grid, const evd_species* species, void* stream, void* pa,
@@ -789,6 +858,7 @@ evd_status evd_destroy(evd_ctx* c)
     }
     if (c->small) cudaFree(c->small);
     if (c->staging) cudaFree(c->staging);
+    if (c->lumps) cudaFree(c->lumps);
     delete c;
     return EVD_OK;
 }

@@ -82,8 +82,8 @@ cudaError_t dispatch_init(const HostParams& h, const double* x, const double* n,
     template <>                                                                                       \
     cudaError_t launch_step_tma<PREC>(const HostParams& h, const void* maps, const void* fin,         \
                                       void* fout, double* mp, unsigned* err, int flags,               \
-                                      const double* corr, cudaStream_t st)                            \
+                                      const double* corr, const float* lumps, cudaStream_t st)        \
     {                                                                                                 \
-        return dispatch_step_tma<S>(h, maps, fin, fout, mp, err, flags, corr, st);                    \
+        return dispatch_step_tma<S>(h, maps, fin, fout, mp, err, flags, corr, lumps, st);             \
     }                                                                                                 \
     }

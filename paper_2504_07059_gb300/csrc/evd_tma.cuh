@@ -28,9 +28,12 @@
 // Walls: a thread's (x, y) column is fixed for the whole march, so solid
 // in-plane stencil nodes are removed once, by zeroing their weights; a z-slab
 // beyond a z wall contributes nothing.  Wall-adjacent nodes add the App. A
-// lumped terms, for which they read their own two populations from global
-// memory.  Periodic z is a wrapped slab coordinate; x and y must be walled
-// (other geometries use the general kernel).
+// lumped terms f_a += L_self f*_a(O) + L_opp f*_abar(O), with the coefficients
+// of their wall class (which of the six walls they touch) from a table built
+// on the host, and their own populations f*(O) fetched from global memory at
+// the start of the iteration so that the loads overlap the interpolation.
+// Periodic z is a wrapped slab coordinate; x and y must be walled (other
+// geometries use the general kernel).
 #pragma once
 
 #include <cuda.h>
@@ -225,7 +228,7 @@ template <int NS, typename S, int TY, int SLOTS>
 __global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
-           const double* __restrict__ corr, int ntx, int nty, int zchunk)
+           const double* __restrict__ corr, const float2* __restrict__ lumps, int ntx, int nty, int zchunk)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int Q = 19;
@@ -300,6 +303,8 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     const bool col_wall = xlo || xhi || ylo || yhi;
     const MaskedW mx = masked_weights(w, xlo, xhi), my = masked_weights(w, ylo, yhi);
     const int nxy = p.nx * p.ny;
+    const int pstride = (int)p.pstride;   // the host guarantees NS * 19 * pstride < 2^31
+    const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
 
     // running sums: z-moving directions (A: node at z = k-1, B: node at k),
     // in-plane directions (N: value at z = k-1)
@@ -313,13 +318,23 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     for (int idx = 0; idx < nstage; ++idx) {
         const int k = kfirst + idx;
         const int slot = idx % SLOTS;
-        const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
         const unsigned char* base = smem + slot * G::slot_bytes;
         const bool halo = stage_is_halo(k, zb, ze);
         const bool solid_slab = zwall && (k < 0 || k >= p.nz);
         const int zo = k - 1;                   // node finished this iteration
         const bool emit = zo >= zb && zo < ze;  // the same for every thread of the CTA
-        float f[Q];
+        const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
+        const int node = x + p.nx * y + nxy * zo;
+        const bool wall_node = emit && active && (col_wall || zlo || zhi);
+        float f[Q], cen[Q];
+        if (wall_node) {
+            // the node's own post-collision populations, for the App. A terms
+            static_for<1, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                cen[A] = (float)fin[plane_of<1, NS>(sp, A) * pstride + node];
+            });
+        }
+        const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
         if (ok) {
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
@@ -342,22 +357,15 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 
         // ---- node (x, y, zo): wall terms, correction, moments
         float rho = 1.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
-        const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
-        const int node = x + p.nx * y + nxy * zo;
         if (ok && emit) {
-            if (active && (col_wall || zlo || zhi)) {
-                Nbr nb;
-                nb.lo[0] = xlo; nb.hi[0] = xhi; nb.lo[1] = ylo; nb.hi[1] = yhi; nb.lo[2] = zlo; nb.hi[2] = zhi;
+            if (wall_node) {
+                const float2* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
                 static_for<1, Q>([&](auto ac) {
                     constexpr int A = decltype(ac)::value;
                     constexpr int AB = opp<1>(A);
                     const float ref = ref_c[wclass<1>(A)];
-                    const float ls = lumped<1, A>(p, sp, nb, true);
-                    const float lo = lumped<1, AB>(p, sp, nb, false);
-                    const long long pa = (long long)plane_of<1, NS>(sp, A) * p.pstride + node;
-                    const long long pb = (long long)plane_of<1, NS>(sp, AB) * p.pstride + node;
-                    if (ls != 0.0f) f[A] += ls * ((float)fin[pa] + ref);
-                    if (lo != 0.0f) f[A] += lo * ((float)fin[pb] + ref);
+                    const float2 l = __ldg(L + A);
+                    f[A] += l.x * (cen[A] + ref) + l.y * (cen[AB] + ref);
                 });
             }
             if (corr) {
@@ -380,7 +388,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             });
             if (active && !(r > 0.0f)) err |= ERR_RHO;
             rho = r;
-            const float rinv = 1.0f / r;
+            const float rinv = __fdividef(1.0f, r);
 #pragma unroll
             for (int d = 0; d < 3; ++d) ueq[d] = csp * j[d] * rinv + 0.5f * p.g[d];
             exch[((idx & 1) * NS * TY + sp * TY + ty) * TTX + tx] = make_float4(rho, ueq[0], ueq[1], ueq[2]);
@@ -401,7 +409,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float rho_m = 0.0f, n = 0.0f;
 #pragma unroll
         for (int i = 0; i < NS; ++i) { rho_m += r[i]; n += r[i] * p.Minv[i]; }
-        const float rinv_m = 1.0f / rho_m;
+        const float rinv_m = __fdividef(1.0f, rho_m);
         float u[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -413,7 +421,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float X[MAXS][MAXS] = {};
         if constexpr (NS == 2) {
             const float A12 = (r[0] + r[1]) * p.iD[0][1] + n * p.MM[0][1];
-            X[0][1] = X[1][0] = 2.0f * rho_m * p.iD[0][1] / A12;
+            X[0][1] = X[1][0] = __fdividef(2.0f * rho_m * p.iD[0][1], A12);
         } else if constexpr (NS == 3) {
             const float A12 = (r[0] + r[1]) * p.iD[0][1] + n * p.MM[0][1];
             const float A13 = (r[0] + r[2]) * p.iD[0][2] + n * p.MM[0][2];
@@ -421,10 +429,10 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             const float B12 = 2.0f * rho_m * p.iD[0][1];
             const float B13 = 2.0f * rho_m * p.iD[0][2];
             const float B23 = 2.0f * rho_m * p.iD[1][2];
-            const float rA13 = 1.0f / A13;
-            const float X23 = (B23 - r[0] * B13 * rA13 * p.iD[1][2]) /
-                              (A23 - r[0] * r[1] * rA13 * p.iD[0][2] * p.iD[1][2]);
-            X[0][1] = X[1][0] = (B12 - r[2] * X23 * p.iD[0][1]) / A12;
+            const float rA13 = __fdividef(1.0f, A13);
+            const float X23 = __fdividef(B23 - r[0] * B13 * rA13 * p.iD[1][2],
+                                         A23 - r[0] * r[1] * rA13 * p.iD[0][2] * p.iD[1][2]);
+            X[0][1] = X[1][0] = __fdividef(B12 - r[2] * X23 * p.iD[0][1], A12);
             X[0][2] = X[2][0] = (B13 - r[1] * X23 * p.iD[0][2]) * rA13;
             X[1][2] = X[2][1] = X23;
         }
@@ -473,7 +481,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             const float S_ = p.wl[C] * sr * fmaf(csp * eg, 1.0f + t1, -ug);
             const float fs = fmaf(omt, f[A], fmaf(feq, B, S_));
             if (active)
-                Codec<S>::st(fout + (long long)plane_of<1, NS>(sp, A) * p.pstride + node, fs - ref_c[C]);
+                Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - ref_c[C]);
         });
     }
 
