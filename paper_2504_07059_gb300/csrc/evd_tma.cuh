@@ -1,17 +1,16 @@
 // evd_tma.cuh -- the D3Q19 step with TMA-staged tiles (float / half storage).
 //
 // Work decomposition.  A CTA owns a column of TX x TY nodes in (x, y) and a
-// chunk of z.  It has one compute thread per (node, species) -- warp w <
-// TY*NS holds the 32 x-nodes of row w % TY for species w / TY -- and one
-// producer warp.  The CTA marches up its z-chunk.  For every z-plane the
-// producer brings, with one TMA tile copy (cp.async.bulk.tensor) per storage
-// group, the slabs of every (species, direction) plane into a ring of SLOTS
-// shared-memory stages: the tile plus a one-node halo along the in-plane
-// dimensions the group's directions move in.  Each stage has a "full"
-// mbarrier (completed by the copies' transaction bytes) and an "empty"
-// mbarrier (one arrival per compute warp once it has read the stage), so the
-// producer runs up to SLOTS stages ahead and the compute warps never wait for
-// copies to be issued.
+// chunk of z, with one thread per (node, species): warp w holds the 32
+// x-nodes of row w % TY for species w / TY.  The CTA marches up its z-chunk.
+// For every z-plane, one TMA tile copy (cp.async.bulk.tensor) per storage
+// group brings the slabs of every (species, direction) plane into a ring of
+// SLOTS shared-memory stages: the tile plus a one-node halo along the
+// in-plane dimensions the group's directions move in.  Each stage completes
+// on its own mbarrier (transaction bytes).  The copies for stage idx+SLOTS-1
+// are issued by seven lanes of warp 0 at the top of iteration idx, into the
+// slot every warp finished reading before the previous iteration's barrier,
+// so SLOTS-1 stages are in flight while one is computed.
 //
 // Each slab is read once: its in-plane interpolation R (1, 3 or 3x3 points of
 // Eq. Second_order_spatial_interpolation) is formed in registers, then
@@ -82,9 +81,8 @@ struct TmaLayout {
     static constexpr int exch_bytes = 2 * NS * TY * TTX * 16;   // two float4 buffers
     static constexpr int msum_offset = ring_bytes + exch_bytes;
     static constexpr int bar_offset = msum_offset + NS * TY * 8 + 8;
-    static constexpr int total_bytes = bar_offset + 2 * SLOTS * 8 + 128;   // + alignment slack
-    static constexpr int consumers = TTX * TY * NS;
-    static constexpr int threads = consumers + 32;
+    static constexpr int total_bytes = bar_offset + SLOTS * 8 + 128;   // + alignment slack
+    static constexpr int threads = TTX * TY * NS;
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -100,10 +98,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(unsigned bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
 {
@@ -138,20 +132,7 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// Barrier 1 among the compute warps only, returning the OR of v over them.
-__device__ __forceinline__ bool consumers_sync_or(bool v, int nthreads)
-{
-    unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((unsigned)v), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 struct TmaMaps {
     CUtensorMap m[NGRP];   // one per storage group of the input buffer
@@ -239,7 +220,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + G::bar_offset);
     const unsigned ring = smem_u32(smem);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
-    auto empty = [&](int s) { return smem_u32(&bars[SLOTS + s]); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x % (ntx * nty);
@@ -252,42 +232,33 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     const int nstage = ze - zb + 2;   // stages k = zb-1 .. ze
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SLOTS; ++s) {
-            mbar_init(full(s), 1);
-            mbar_init(empty(s), TY * NS);
-        }
+        for (int s = 0; s < SLOTS; ++s) mbar_init(full(s), 1);
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (warp == TY * NS) {
-        // ------------------------------------------------------ producer
-        const int g = lane;   // lanes 0..6 each own one storage group
-        const int cls = grp_cls(g < NGRP ? g : 0);
-        const int cx = (cls & 1) ? x0 - G::XP : x0;
-        const int cy = (cls & 2) ? y0 - 1 : y0;
-        const int c3 = NS * grp_start(g < NGRP ? g : 0);
-        const unsigned goff = (unsigned)G::group_offset(g < NGRP ? g : 0);
-        const bool moves_z = g < NGRP && grp_moves_z(g);
-        bool ok = true;
-        for (int idx = 0; idx < nstage && ok; ++idx) {
-            const int slot = idx % SLOTS;
-            if (idx >= SLOTS) ok = mbar_wait_bounded(empty(slot), (unsigned)(((idx / SLOTS) - 1) & 1));
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            const int k = kfirst + idx;
-            const bool halo = stage_is_halo(k, zb, ze);
-            const int zc = zwall ? k : (k % p.nz + p.nz) % p.nz;   // walled: out of range -> zero fill
-            if (lane == 0) mbar_arrive_expect_tx(full(slot), (unsigned)G::stage_bytes(halo));
-            __syncwarp();
-            if (g < NGRP && (!halo || moves_z))
-                tma_load_4d(ring + (unsigned)(slot * G::slot_bytes) + goff, &maps.m[g], cx, cy, zc, c3, full(slot));
-        }
-        if (!ok && lane == 0) atomicOr(err_flag, ERR_TIMEOUT);
-        return;
-    }
+    // copy parameters of the storage group this lane of warp 0 issues
+    const int g = lane < NGRP ? lane : 0;
+    const int gcls = grp_cls(g);
+    const int gcx = (gcls & 1) ? x0 - G::XP : x0;
+    const int gcy = (gcls & 2) ? y0 - 1 : y0;
+    const int gc3 = NS * grp_start(g);
+    const unsigned goff = (unsigned)G::group_offset(g);
+    const bool gz = grp_moves_z(g);
+    const bool issuer = warp == 0 && lane < NGRP;
+    auto issue = [&](int idx) {
+        const int slot = idx % SLOTS;
+        const int k = kfirst + idx;
+        const bool halo = stage_is_halo(k, zb, ze);
+        const int zc = zwall ? k : (k % p.nz + p.nz) % p.nz;   // walled: out of range -> zero fill
+        if (lane == 0) mbar_arrive_expect_tx(full(slot), (unsigned)G::stage_bytes(halo));
+        if (!halo || gz) tma_load_4d(ring + (unsigned)(slot * G::slot_bytes) + goff, &maps.m[g], gcx, gcy, zc, gc3,
+                                     full(slot));
+    };
+    if (issuer)
+        for (int idx = 0; idx < SLOTS - 1 && idx < nstage; ++idx) issue(idx);
 
-    // ------------------------------------------------------------ consumers
+    // ------------------------------------------------------------ compute
     const int ty = warp % TY, sp = warp / TY;
     const int tx = lane;
     const int x = x0 + tx, y = y0 + ty;
@@ -318,6 +289,11 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     for (int idx = 0; idx < nstage; ++idx) {
         const int k = kfirst + idx;
         const int slot = idx % SLOTS;
+        if (issuer && idx + SLOTS - 1 < nstage) {
+            // the slot of stage idx-1, read by every warp before the last barrier
+            fence_proxy_async();
+            issue(idx + SLOTS - 1);
+        }
         const unsigned char* base = smem + slot * G::slot_bytes;
         const bool halo = stage_is_halo(k, zb, ze);
         const bool solid_slab = zwall && (k < 0 || k >= p.nz);
@@ -352,8 +328,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                 }
             });
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty(slot));   // this warp is done with the stage
 
         // ---- node (x, y, zo): wall terms, correction, moments
         float rho = 1.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
@@ -393,9 +367,9 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             for (int d = 0; d < 3; ++d) ueq[d] = csp * j[d] * rinv + 0.5f * p.g[d];
             exch[((idx & 1) * NS * TY + sp * TY + ty) * TTX + tx] = make_float4(rho, ueq[0], ueq[1], ueq[2]);
         }
-        // one barrier of the compute warps per iteration: the exchange, and
-        // agreement on a failed wait
-        failed = consumers_sync_or(!ok, G::consumers);
+        // one barrier per iteration: the exchange, the release of the stage
+        // just read, and agreement on a failed wait
+        failed = __syncthreads_or(!ok);
         if (failed) break;
         if (!emit) continue;
 
@@ -486,8 +460,11 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     }
 
     if (failed) {
-        // never expected: report and leave (the producer gives up as well)
-        if (threadIdx.x == 0) atomicOr(err_flag, ERR_TIMEOUT);
+        // never expected: report, let copies still in flight land, and leave
+        if (threadIdx.x == 0) {
+            atomicOr(err_flag, ERR_TIMEOUT);
+            for (int q = 0; q < SLOTS; ++q) (void)mbar_wait_bounded(full(q), 0u);
+        }
         return;
     }
     if (err) atomicOr(err_flag, err);
@@ -497,7 +474,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) msum[sp * TY + ty] = v;
-        (void)consumers_sync_or(false, G::consumers);
+        __syncthreads();
         if (threadIdx.x < NS) {
             double t = 0.0;
 #pragma unroll
