@@ -232,6 +232,8 @@ def run_ours(args) -> None:
 
     stream = torch.cuda.current_stream(dev)
     sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, prec, stream)
+    if args.tile_rows:
+        evd.evd_set_tile_rows(sim.ctx, args.tile_rows)
     # inputs resident in HBM before the timed region
     x_dev = torch.from_numpy(np.ascontiguousarray(wl.x)).to(dev)
     evd.evd_set_fields_device(sim.ctx, x_dev, None)
@@ -336,6 +338,7 @@ def main():
     ap.add_argument("--size", type=int, default=256, help="cube side of the stratification workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (2 or 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -22,6 +22,7 @@ namespace {
 constexpr int FLAG_MASS = 1, FLAG_RAW = 2;   // must match the device-side flags
 constexpr int BLOCK = 128;                   // must match the device-side block size
 constexpr long long PLANE_ALIGN = 64;        // elements; every plane starts 128-byte aligned
+constexpr int kTmaRows = 4;                  // default rows per tile of the TMA step
 
 thread_local std::string g_create_error;
 
@@ -55,6 +56,7 @@ struct evd_ctx {
     bool tma_ok;         // the TMA-staged step can run this configuration
     int kernel;          // EVD_KERNEL_GENERAL or EVD_KERNEL_TMA
     int tma_blocks;      // grid of the TMA step
+    int tma_ty;          // rows per tile of the TMA step (2 or 4)
     int last_parts;      // mass partials written by the last measuring launch
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
@@ -244,8 +246,8 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
         const int in = (fin == c->buf[0]) ? 0 : 1;
         c->last_parts = c->tma_blocks;
         if (c->precision == EVD_FP32)
-            return evd::launch_step_tma<1>(h, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
-        return evd::launch_step_tma<2>(h, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
+            return evd::launch_step_tma<1>(h, c->tma_ty, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
+        return evd::launch_step_tma<2>(h, c->tma_ty, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
     }
     c->last_parts = c->nblocks;
     switch (c->precision * 2 + c->lattice) {
@@ -463,7 +465,7 @@ bool tma_setup(evd_ctx* c)
             return false;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    const int TY = evd::TmaLaunch::TY, TX = evd::TmaLaunch::TX;
+    const int TY = c->tma_ty, TX = evd::TmaLaunch::TX;
     const int XP = (int)(16 / elem);
     // storage groups: halo class (bit 0 x, bit 1 y) and number of directions
     const int gcls[7] = {0, 0, 1, 1, 2, 2, 3};
@@ -530,10 +532,13 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
             }
         }
     }
+    c->tma_ty = kTmaRows;
     c->tma_ok = tma_setup(c);
     c->kernel = c->tma_ok ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL;
-    c->tma_blocks = c->tma_ok ? evd::TmaLaunch::grid(c->hp) : 0;
-    const int max_parts = c->nblocks > c->tma_blocks ? c->nblocks : c->tma_blocks;
+    c->tma_blocks = c->tma_ok ? evd::TmaLaunch::grid(c->hp, c->tma_ty) : 0;
+    // partials for either tile height, so that evd_set_tile_rows never reallocates
+    const int max_tma = c->tma_ok ? evd::TmaLaunch::grid(c->hp, 2) : 0;
+    const int max_parts = c->nblocks > max_tma ? c->nblocks : max_tma;
     const size_t part_bytes = ((size_t)max_parts * c->ns * sizeof(double) + 255) / 256 * 256;
     e = cudaMalloc(&c->small, part_bytes + 5 * 256);
     if (e != cudaSuccess) {
@@ -826,6 +831,26 @@ evd_status evd_set_kernel(evd_ctx* c, int kernel)
 }
 
 int evd_get_kernel(const evd_ctx* c) { return c ? c->kernel : 0; }
+
+evd_status evd_set_tile_rows(evd_ctx* c, int rows)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (rows != 2 && rows != 4) return fail(c, EVD_ERR_ARG, "rows must be 2 or 4");
+    if (!c->tma_ok) return fail(c, EVD_ERR_ARG, "the TMA-staged step does not apply to this configuration");
+    if (rows == c->tma_ty) return EVD_OK;
+    DeviceGuard dg(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    const int old = c->tma_ty;
+    if (c->lumps) { cudaFree(c->lumps); c->lumps = nullptr; }
+    c->tma_ty = rows;
+    if (!tma_setup(c)) {
+        c->tma_ty = old;
+        tma_setup(c);
+        return fail(c, EVD_ERR_CUDA, "could not rebuild the tile copies");
+    }
+    c->tma_blocks = evd::TmaLaunch::grid(c->hp, rows);
+    return EVD_OK;
+}
 
 evd_status evd_set_mass_correction(evd_ctx* c, int every)
 {

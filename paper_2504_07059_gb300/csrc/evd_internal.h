@@ -50,11 +50,12 @@ inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + bloc
 // maps points to the seven tensor maps (CUtensorMap, 128 bytes each) of the
 // input buffer, one per storage group of directions.
 struct TmaLaunch {
-    static constexpr int TX = 32, TY = 4, SLOTS = 4, NGROUPS = 7;
+    static constexpr int TX = 32, SLOTS = 4, NGROUPS = 7;
+    // rows per tile: 4 (one CTA per SM) or 2 (two CTAs per SM)
     static int zchunk(const HostParams& h) { return h.nz < 32 ? h.nz : 32; }
-    static int grid(const HostParams& h)
+    static int grid(const HostParams& h, int ty)
     {
-        const int ntx = (h.nx + TX - 1) / TX, nty = (h.ny + TY - 1) / TY, zc = zchunk(h);
+        const int ntx = (h.nx + TX - 1) / TX, nty = (h.ny + ty - 1) / ty, zc = zchunk(h);
         return ntx * nty * ((h.nz + zc - 1) / zc);
     }
 };
@@ -63,7 +64,7 @@ struct TmaLaunch {
 // float pairs; wall class = cx + 3 cy + 9 cz with c = 0 interior, 1 at the
 // low wall, 2 at the high wall of that dimension.
 template <int PREC>
-cudaError_t launch_step_tma(const HostParams& h, const void* maps, const void* fin, void* fout,
+cudaError_t launch_step_tma(const HostParams& h, int ty, const void* maps, const void* fin, void* fout,
                             double* mass_part, unsigned* err, int flags, const double* corr,
                             const float* lumps, cudaStream_t st);
 

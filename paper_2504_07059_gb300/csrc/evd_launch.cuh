@@ -80,10 +80,10 @@ cudaError_t dispatch_init(const HostParams& h, const double* x, const double* n,
 #define EVD_DEFINE_TMA_LAUNCHER(PREC, S)                                                              \
     namespace evd {                                                                                   \
     template <>                                                                                       \
-    cudaError_t launch_step_tma<PREC>(const HostParams& h, const void* maps, const void* fin,         \
+    cudaError_t launch_step_tma<PREC>(const HostParams& h, int ty, const void* maps, const void* fin, \
                                       void* fout, double* mp, unsigned* err, int flags,               \
                                       const double* corr, const float* lumps, cudaStream_t st)        \
     {                                                                                                 \
-        return dispatch_step_tma<S>(h, maps, fin, fout, mp, err, flags, corr, lumps, st);             \
+        return dispatch_step_tma<S>(h, ty, maps, fin, fout, mp, err, flags, corr, lumps, st);         \
     }                                                                                                 \
     }

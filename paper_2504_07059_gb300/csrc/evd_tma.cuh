@@ -206,7 +206,7 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
 }
 
 template <int NS, typename S, int TY, int SLOTS>
-__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, 1)
+__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
            const double* __restrict__ corr, const float2* __restrict__ lumps, int ntx, int nty, int zchunk)

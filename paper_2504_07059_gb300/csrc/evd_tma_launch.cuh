@@ -6,11 +6,11 @@
 
 namespace evd {
 
-template <int NS, typename S>
+template <int NS, typename S, int TY>
 cudaError_t launch_tma_ns(const HostParams& h, const TmaMaps& maps, const void* fin, void* fout, double* mp,
                           unsigned* err, int flags, const double* corr, const float* lumps, cudaStream_t st)
 {
-    constexpr int TY = TmaLaunch::TY, SLOTS = TmaLaunch::SLOTS;
+    constexpr int SLOTS = TmaLaunch::SLOTS;
     using L = TmaLayout<NS, S, TY, SLOTS>;
     auto kern = k_step_tma<NS, S, TY, SLOTS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::total_bytes);
@@ -18,22 +18,26 @@ cudaError_t launch_tma_ns(const HostParams& h, const TmaMaps& maps, const void* 
     const Params<float> p = to_params<float>(h);
     const int ntx = (h.nx + TTX - 1) / TTX, nty = (h.ny + TY - 1) / TY;
     const dim3 block(L::threads);
-    kern<<<TmaLaunch::grid(h), block, L::total_bytes, st>>>(maps, p, (const S*)fin, (S*)fout, mp, err, flags,
+    kern<<<TmaLaunch::grid(h, TY), block, L::total_bytes, st>>>(maps, p, (const S*)fin, (S*)fout, mp, err, flags,
                                                             corr, (const float2*)lumps, ntx, nty,
                                                             TmaLaunch::zchunk(h));
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t dispatch_step_tma(const HostParams& h, const void* maps, const void* fin, void* fout, double* mp,
-                              unsigned* err, int flags, const double* corr, const float* lumps, cudaStream_t st)
+cudaError_t dispatch_step_tma(const HostParams& h, int ty, const void* maps, const void* fin, void* fout,
+                              double* mp, unsigned* err, int flags, const double* corr, const float* lumps,
+                              cudaStream_t st)
 {
     if (h.lattice != 1 || !h.wall[0] || !h.wall[1]) return cudaErrorInvalidValue;
     const TmaMaps& m = *reinterpret_cast<const TmaMaps*>(maps);
-    switch (h.ns) {
-        case 1: return launch_tma_ns<1, S>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
-        case 2: return launch_tma_ns<2, S>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
-        case 3: return launch_tma_ns<3, S>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+    switch (h.ns * 8 + ty) {
+        case 1 * 8 + 2: return launch_tma_ns<1, S, 2>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+        case 2 * 8 + 2: return launch_tma_ns<2, S, 2>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+        case 3 * 8 + 2: return launch_tma_ns<3, S, 2>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+        case 1 * 8 + 4: return launch_tma_ns<1, S, 4>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+        case 2 * 8 + 4: return launch_tma_ns<2, S, 4>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
+        case 3 * 8 + 4: return launch_tma_ns<3, S, 4>(h, m, fin, fout, mp, err, flags, corr, lumps, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "evd_launch_count": (ctypes.c_longlong, [_vp]),
     "evd_set_kernel": (_st, [_vp, ctypes.c_int]),
     "evd_get_kernel": (ctypes.c_int, [_vp]),
+    "evd_set_tile_rows": (_st, [_vp, ctypes.c_int]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
@@ -253,6 +254,10 @@ def evd_set_kernel(ctx, kernel: int):
 
 def evd_get_kernel(ctx) -> int:
     return lib().evd_get_kernel(ctx)
+
+
+def evd_set_tile_rows(ctx, rows: int):
+    _check(lib().evd_set_tile_rows(ctx, int(rows)), ctx)
 
 
 def evd_set_mass_correction(ctx, every: int):

@@ -28,24 +28,27 @@ CASES = {
 }
 
 
-def _run(evd, wl, steps, precision, kernel):
+def _run(evd, wl, steps, precision, kernel, rows=4):
     sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, precision)
     evd.evd_set_kernel(sim.ctx, kernel)
     assert evd.evd_get_kernel(sim.ctx) == kernel
+    if kernel == evd.EVD_KERNEL_TMA:
+        evd.evd_set_tile_rows(sim.ctx, rows)
     sim.set_fields(wl.x, wl.n)
     sim.step(steps)
     return sim
 
 
+@pytest.mark.parametrize("rows", [4, 2])
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_tma_step_matches_oracle(evd, name, precision):
+def test_tma_step_matches_oracle(evd, name, precision, rows):
     make, steps = CASES[name]
     wl = make()
     if precision == "fp16" and wl.shape[0] % 8:
         pytest.skip("rows must be a multiple of 16 bytes for TMA")
     o = oracle_run(wl, steps)
-    sim = _run(evd, wl, steps, precision, evd.EVD_KERNEL_TMA)
+    sim = _run(evd, wl, steps, precision, evd.EVD_KERNEL_TMA, rows)
     ob = o.observables()
     x = sim.mole_fractions()
     assert np.abs(x - ob["x"]).max() < TOL_X[precision], np.abs(x - ob["x"]).max()
@@ -65,8 +68,10 @@ def test_tma_and_general_kernels_agree(evd, name):
     wl = make()
     a = _run(evd, wl, steps, "fp32", evd.EVD_KERNEL_TMA)
     b = _run(evd, wl, steps, "fp32", evd.EVD_KERNEL_GENERAL)
-    fa, fb = a.populations(), b.populations()
+    c = _run(evd, wl, steps, "fp32", evd.EVD_KERNEL_TMA, rows=2)
+    fa, fb, fc = a.populations(), b.populations(), c.populations()
     assert max_rel(fa, fb) < 1e-5
+    assert np.array_equal(fa, fc)          # tile shape does not change the arithmetic
     assert max_rel(a.species_mass(), b.species_mass()) < 1e-6
 
 
