@@ -193,9 +193,10 @@ long long evd_launch_count(const evd_ctx* ctx);
 evd_status evd_set_kernel(evd_ctx* ctx, int kernel);
 int evd_get_kernel(const evd_ctx* ctx);
 
-/* Rows per tile of the TMA-staged step: 4 (one CTA of 12 warps per SM for
- * three species) or 2 (two smaller CTAs per SM).  Same results; a tuning
- * knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not apply. */
+/* Rows per tile of the TMA-staged step: 2 (the default; two CTAs of 6 warps
+ * per SM for three species) or 4 (one CTA of 12 warps per SM).  Same results;
+ * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not
+ * apply. */
 evd_status evd_set_tile_rows(evd_ctx* ctx, int rows);
 
 /* FP64 species-mass correction (not in the paper; a precision device for

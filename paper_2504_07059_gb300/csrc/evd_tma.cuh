@@ -205,6 +205,22 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
     }
 }
 
+// Unit lattice speed off the walls: weights (1, 0, 0), the upstream node.
+template <int A, int NS, typename S, int TY, int SLOTS>
+__device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float ref)
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
+    constexpr int g = grp<1>(A);
+    constexpr int cls = grp_cls(g);
+    constexpr int W = G::bw(cls);
+    const S* s = reinterpret_cast<const S*>(slot + G::group_offset(g)) +
+                 (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
+    const int cx = tx + ((cls & 1) ? G::XP : 0) - ex;
+    const int cy = ty + ((cls & 2) ? 1 : 0) - ey;
+    return (float)s[cy * W + cx] + ref;
+}
+
 template <int NS, typename S, int TY, int SLOTS>
 __global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
@@ -273,6 +289,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     const bool ylo = p.wall[1] && y == 0, yhi = p.wall[1] && y == p.ny - 1;
     const bool col_wall = xlo || xhi || ylo || yhi;
     const MaskedW mx = masked_weights(w, xlo, xhi), my = masked_weights(w, ylo, yhi);
+    const bool unit_fast = p.unit[sp] && !col_wall;
     const int nxy = p.nx * p.ny;
     const int pstride = (int)p.pstride;   // the host guarantees NS * 19 * pstride < 2^31
     const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
@@ -311,7 +328,24 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             });
         }
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
-        if (ok) {
+        if (ok && unit_fast) {
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                constexpr int ez = ev<1>(A, 2);
+                const float ref = ref_c[wclass<1>(A)];
+                if constexpr (ez == 0) {
+                    f[A] = accN[A];
+                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                } else if constexpr (ez > 0) {
+                    // exact shift: node z takes slab z - 1, which arrived two iterations ago
+                    f[A] = accA[A];
+                    accA[A] = accB[A];
+                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                } else {
+                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                }
+            });
+        } else if (ok) {
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
