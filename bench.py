@@ -42,10 +42,14 @@ METRIC = "species-site updates/s (GLUPS)"
 UNIT = "GLUPS"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch, from an
-# ncu capture of the kernel source with this digest (see profiles/).  A kernel
+# dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel launch, keyed
+# by (kernel source digest, workload, cube side, precision), from an ncu
+# capture of the kernel source with this digest (summaries under profiles/).  A kernel
 # change changes the digest and the entry no longer applies.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 128^3 capture: 536.0 MB read + 436.7 MB written; x8 for a 256^3 launch
+    ("036c0521bf632737", "stratification", 256, "fp32"): 7781.4e6,
+}
 
 
 def kernel_digest() -> str:
@@ -274,7 +278,7 @@ def run_ours(args) -> None:
     bpl = bytes_per_ssu(wl, prec) * ns * nsites
     achieved = bpl / (ms / args.steps * 1e-3) / 1e9
     digest = kernel_digest()
-    traffic = NCU_TRAFFIC.get((digest, args.workload, prec))
+    traffic = NCU_TRAFFIC.get((digest, args.workload, args.size, prec))
 
     # end to end through the public API with pinned host buffers: upload the
     # initial mole fractions, run the same number of steps, read the mole
@@ -297,8 +301,30 @@ def run_ours(args) -> None:
     h2d = x_host.numel() * 8
     d2h = out_host.numel() * 8
 
-    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    kernel_name = "k_step_tma" if evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_TMA else "k_step"
     sim.close()
+
+    # the same workload advanced by the plain FP64 step on the same GPU (a few
+    # steps; the FP64 path is ALU-bound on this part)
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64:
+        s64 = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp64", stream)
+        evd.evd_set_fields_device(s64.ctx, x_dev, None)
+        n64 = max(3, min(args.steps, 20))
+        evd.evd_step(s64.ctx, 3)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        evd.evd_step(s64.ctx, n64)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        evd.evd_check(s64.ctx)
+        ms64 = a.elapsed_time(b) / n64
+        s64.close()
+        fp64 = {"ms_per_step": ms64, "value": ns * nsites / (ms64 * 1e-3) / 1e9, "unit": UNIT,
+                "steps": n64, "speedup": ms64 / (ms / args.steps)}
+
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         cl = clocks.summary()
         out = {
@@ -312,7 +338,9 @@ def run_ours(args) -> None:
                            else "working set fits in L2 (HBM fraction not meaningful)"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "k_step", "bytes_per_launch": bpl},
+                         "kernel": kernel_name, "bytes_per_launch": bpl,
+                         "timing": "CUDA events around the timed steps, divided by the steps "
+                                   "(includes the small mass-correction reductions)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps_per_e2e_step": args.steps,
                     "what": "evd_set_fields(pinned host x) + evd_step(steps) + "
@@ -320,6 +348,8 @@ def run_ours(args) -> None:
             "gpu_launches": launches,
             "clocks": cl,
         }
+        if fp64 is not None:
+            out["vs_fp64_gpu"] = fp64
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)
@@ -338,6 +368,7 @@ def main():
     ap.add_argument("--size", type=int, default=256, help="cube side of the stratification workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 step for comparison")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (2 or 4)")
     args = ap.parse_args()
     if args.warmup < 3:
