@@ -216,6 +216,22 @@ def run_reference(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+def replica_throughput(ms_local: float, ssu_rank: int, device) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: every rank processed
+    ``ssu_rank`` species-site updates in ``ms_local`` milliseconds; the job
+    takes as long as the slowest rank.  Returns (max ms over ranks, GLUPS of
+    all ranks together).  With torch.distributed initialised this is one MAX
+    all-reduce on ``device`` (NCCL on the GPU, gloo on CPU); otherwise one rank."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * ssu_rank / (ms_max * 1e-3) / 1e9
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -265,12 +281,8 @@ def run_ours(args) -> None:
     evd.evd_check(sim.ctx)
     launches = evd.evd_launch_count(sim.ctx) - launches0
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     ssu_rank = ns * nsites * args.steps
-    value = world * ssu_rank / (ms_max * 1e-3) / 1e9
+    ms_max, value = replica_throughput(ms, ssu_rank, dev)
 
     # roofline of the dominant (only) kernel of the step: algorithmic bytes per
     # launch over the average launch duration (one launch per step)
@@ -294,10 +306,7 @@ def run_ours(args) -> None:
         evd.evd_get_mole_fractions(sim.ctx, out_host)
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = min(e2e_times) if e2e_times else float("nan")
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * ssu_rank / float(e2e_t.item()) / 1e9
+    _, e2e_value = replica_throughput(e2e_s * 1e3, ssu_rank, dev)
     h2d = x_host.numel() * 8
     d2h = out_host.numel() * 8
 
