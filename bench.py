@@ -185,9 +185,57 @@ def cpu_baseline(budget_s: float = 15.0) -> dict:
                       f"single-threaded C, {dt:.1f} s"}
 
 
+def time_oracle_tubes(budget_s: float, steps: int | None = None, warmup: int = 0) -> tuple[float, int, str]:
+    """The FP64 oracle on the first tubes of the sweep (same recipe and seed),
+    one after another, until about budget_s seconds of stepping (or ``steps``
+    steps per tube on as many tubes as fit).  Returns (seconds, species-site
+    updates, description)."""
+    from oracle import oracle as O
+    tubes = W.batched_tubes()
+    t_total, ssu, used, k_used = 0.0, 0, 0, 0
+    for wl in tubes:
+        o = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+        o.init(wl.x)
+        if warmup:
+            o.step(warmup)
+        k = steps
+        if k is None:   # as many steps as fit in what is left of the budget, at least 2
+            t0 = time.perf_counter()
+            o.step(1)
+            per = time.perf_counter() - t0
+            t_total += per
+            ssu += wl.ns * wl.nsites
+            k = max(2, int((budget_s - t_total) / max(per, 1e-6)))
+        t0 = time.perf_counter()
+        o.step(k)
+        t_total += time.perf_counter() - t0
+        ssu += wl.ns * wl.nsites * k
+        used += 1
+        k_used = k
+        if t_total >= budget_s:
+            break
+    return t_total, ssu, f"first {used} tube(s) of the sweep, up to {k_used} steps each, FP64 single-threaded C"
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "tubes":
+        # bounded: each step a pass over as many tubes as fit in ~60 s / (W + K)
+        dt, ssu, what = time_oracle_tubes(60.0 / (args.steps + args.warmup) * args.steps)
+        value = ssu / dt / 1e9
+        ssu_step = sum(t.ns * t.nsites for t in W.batched_tubes())
+        out = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ssu_step / (value * 1e9) * 1e3,   # one step of the whole sweep at this rate
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(tubes_config(), precision="fp64", sample=what),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(out), flush=True)
         return
     # choose the sample cube so that warmup + steps end within about a minute
     _, _, per16 = time_oracle_sample(16, 1)
@@ -232,6 +280,117 @@ def replica_throughput(ms_local: float, ssu_rank: int, device) -> tuple[float, f
     return ms_max, world * ssu_rank / (ms_max * 1e-3) / 1e9
 
 
+def tubes_config() -> dict:
+    return {"workload": "batched-tubes-d2q9-512x32", "lattice": "D2Q9", "members": 512, "width": 32,
+            "length": "log-uniform [128, 4096]", "species": "2 or 3", "mass_ratio": "U[1, 10]",
+            "walls": ["y-", "y+"], "seed": W.SEED}
+
+
+def run_tubes(args, torch, dev, world, rank, local) -> None:
+    """The batched sweep: 512 independent tubes advanced by one persistent
+    launch per step, replayed from CUDA graphs, schedule picked by the
+    autotuner before the timed region."""
+    from paper_2504_07059_gb300 import evd
+    tubes = W.batched_tubes()
+    prec = args.precision
+    stream = torch.cuda.current_stream(dev)
+    b = evd.Batch(tubes, prec, stream)
+    x_all = np.concatenate([t.x.ravel() for t in tubes])
+    evd.evd_batch_set_fields(b.b, x_all)   # host path once, for the mass targets
+    t0 = time.perf_counter()
+    sched = evd.evd_batch_autotune(b.b, 8)
+    tune_s = time.perf_counter() - t0
+    ssu_step = sum(t.ns * t.nsites for t in tubes)
+    bpl = sum(t.ns * t.nsites * 2 * 9 * {"fp64": 8, "fp32": 4, "fp16": 2}[prec] for t in tubes)
+    evd.evd_batch_step(b.b, args.warmup)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = evd.evd_batch_launch_count(b.b)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_device_id(torch, local)) as clocks:
+        start.record(stream)
+        evd.evd_batch_step(b.b, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    evd.evd_batch_check(b.b)
+    launches = evd.evd_batch_launch_count(b.b) - launches0
+    ms_max, value = replica_throughput(ms, ssu_step * args.steps, dev)
+    peak, peak_kind = measured_peaks()
+    achieved = bpl / (ms / args.steps * 1e-3) / 1e9
+
+    # end to end through the public API: upload the initial mole fractions
+    # from pinned host memory, run the steps, read the mole fractions back
+    x_host = torch.from_numpy(x_all).pin_memory()
+    out_host = torch.empty_like(x_host).pin_memory()
+    e2e_times = []
+    for _ in range(0 if args.no_e2e else 2):
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        evd.evd_batch_set_fields(b.b, x_host.data_ptr())
+        evd.evd_batch_step(b.b, args.steps)
+        evd.evd_batch_get_mole_fractions(b.b, out_host.data_ptr())
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_s = min(e2e_times) if e2e_times else float("nan")
+    _, e2e_value = replica_throughput(e2e_s * 1e3, ssu_step * args.steps, dev)
+    b.close()
+
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64:
+        b64 = evd.Batch(tubes, "fp64", stream)
+        evd.evd_batch_set_fields(b64.b, x_all)
+        evd.evd_batch_step(b64.b, 8)
+        torch.cuda.synchronize(dev)
+        n64 = 16
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        evd.evd_batch_step(b64.b, n64)
+        z.record(stream)
+        torch.cuda.synchronize(dev)
+        evd.evd_batch_check(b64.b)
+        ms64 = a.elapsed_time(z) / n64
+        b64.close()
+        fp64 = {"ms_per_step": ms64, "value": ssu_step / (ms64 * 1e-3) / 1e9, "unit": UNIT, "steps": n64,
+                "speedup": ms64 / (ms / args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, ssu, what = time_oracle_tubes(15.0)
+        cpu = {"value": ssu / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)"}[prec],
+            "data": "synthetic",
+            "config": dict(tubes_config(), precision=prec, parallelism=f"replicas{world}",
+                           schedule={"item_sites": sched[0], "ctas_per_sm": sched[1], "autotune_s": tune_s},
+                           graph_steps=8, l2="inputs larger than L2 (no flush needed)"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "k_step_batch", "bytes_per_launch": bpl,
+                         "timing": "CUDA events around the timed steps, divided by the steps "
+                                   "(includes the small mass-correction reductions)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": x_host.numel() * 8,
+                    "d2h_bytes_per_step": out_host.numel() * 8, "steps_per_e2e_step": args.steps,
+                    "what": "evd_batch_set_fields(pinned host x) + evd_batch_step(steps) + "
+                            "evd_batch_get_mole_fractions(pinned host)"},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        if fp64 is not None:
+            out["vs_fp64_gpu"] = fp64
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -246,6 +405,11 @@ def run_ours(args) -> None:
 
     from paper_2504_07059_gb300 import build, evd
     build.build()
+    if args.workload == "tubes":
+        run_tubes(args, torch, dev, world, rank, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     wl = make_workload(args.workload, args.size)
     prec = args.precision
     ns, nsites = wl.ns, wl.nsites
@@ -372,7 +536,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stratification", "tube"], default="stratification")
+    ap.add_argument("--workload", choices=["stratification", "tube", "tubes"], default="stratification",
+                    help="stratification: 256^3 D3Q19 closed box; tube: 64x1024 ternary D2Q9 tube; "
+                         "tubes: the batched sweep of 512 D2Q9 tubes")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16"], default="fp32")
     ap.add_argument("--size", type=int, default=256, help="cube side of the stratification workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -39,7 +39,7 @@ def _sources():
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*")) + [os.path.join(INCLUDE, "evd.h"), __file__]):
+    for p in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]):
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode())
             h.update(fh.read())
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     extra = ["-Xptxas", "-v"] if verbose else []
 
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(INCLUDE, "evd.h")]
+        glob.glob(os.path.join(INCLUDE, "*.h"))
     newest_header = max(os.path.getmtime(h) for h in headers)
 
     def compile_one(pair):

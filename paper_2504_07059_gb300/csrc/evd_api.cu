@@ -29,6 +29,7 @@ thread_local std::string g_create_error;
 }  // namespace
 
 void evd::set_thread_error(const std::string& msg) { g_create_error = msg; }
+const char* evd::thread_error() { return g_create_error.c_str(); }
 
 struct evd_ctx {
     HostParams hp;
@@ -100,6 +101,10 @@ evd_status cuda_fail(evd_ctx* c, cudaError_t e, const char* where)
         cudaError_t e_ = (call);                                       \
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
     } while (0)
+
+}  // namespace
+
+namespace evd {
 
 size_t elem_size(int precision)
 {
@@ -227,6 +232,16 @@ void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
         }
     }
 }
+
+}  // namespace evd
+
+namespace {
+
+using evd::buffer_bytes;
+using evd::elem_size;
+using evd::fill_params;
+using evd::plane_stride;
+using evd::validate;
 
 void set_reference(evd_ctx* c, const double* rho_ref)
 {

@@ -1,0 +1,3 @@
+// Batched step kernels, fp32 storage, D3Q19.
+#include "evd_batch_kernels.cuh"
+EVD_DEFINE_BATCH_LAUNCHERS(1, 1, float, float)

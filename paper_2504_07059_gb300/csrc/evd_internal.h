@@ -4,12 +4,16 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <string>
+
+#include "evd.h"
 
 namespace evd {
 
 // Sets the message evd_last_error(NULL) returns on this thread.
 void set_thread_error(const std::string& msg);
+const char* thread_error();
 
 constexpr int MAXS = 3;
 
@@ -30,6 +34,14 @@ struct HostParams {
     double ref[MAXS][3];
 };
 
+// Host-side checks and constants shared by the single-lattice context and the
+// batch of lattices (evd_api.cu).
+size_t elem_size(int precision);
+bool validate(const evd_grid* g, const evd_species* s, std::string& msg);
+long long plane_stride(const evd_grid* g);
+size_t buffer_bytes(const evd_grid* g, const evd_species* s);
+void fill_params(HostParams& h, const evd_grid* g, const evd_species* s);
+
 // Kernel launchers, one explicit specialisation per storage precision
 // (0 double, 1 float deviation, 2 half deviation) and lattice (0 D2Q9,
 // 1 D3Q19), each in its own translation unit.
@@ -42,6 +54,42 @@ struct Launch {
                                const double* corr, cudaStream_t st);
     static cudaError_t init(const HostParams& h, const double* x, const double* n, const double* fsrc,
                             void* fprev, void* fcur, double* mass_part, unsigned* err, cudaStream_t st);
+};
+
+// Batched step: work items are ranges of consecutive sites of one member.
+struct BatchItem {
+    int member, node0, count, ns;
+};
+
+// Where member m lives: element offset of its populations in a population
+// buffer, and offsets of its fields in the concatenated readout arrays.
+struct MemberInfo {
+    long long foff;    // populations (elements)
+    long long xoff;    // x, rho: [ns][sites]
+    long long soff;    // n: [sites]
+    long long uoff;    // u: [D][sites]
+    long long uioff;   // ui: [ns][D][sites]
+    int sites, ns, item_begin, item_end;
+    double M[MAXS];    // molar masses (FP64, for the initial-mass reduction)
+};
+
+struct BatchArgs {
+    const BatchItem* items;
+    int n_items;
+    const void* params;      // Params<T>[members] on the device
+    const MemberInfo* info;  // [members] on the device
+    int grid;                // CTAs of the step launch (persistent when < n_items)
+};
+
+template <int PREC, int LAT>
+struct BatchLaunch {
+    static cudaError_t step(const BatchArgs& a, const void* fin, void* fout, double* part, unsigned* err,
+                            int flags, const double* corr, cudaStream_t st);
+    static cudaError_t readout(const BatchArgs& a, const void* fin, int flags, double* x, double* rho,
+                               double* u, double* ui, double* part, unsigned* err, const double* corr,
+                               cudaStream_t st);
+    static cudaError_t init(const BatchArgs& a, const double* x, const double* n, void* fprev, void* fcur,
+                            double* part, unsigned* err, cudaStream_t st);
 };
 
 inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + block - 1) / block; }

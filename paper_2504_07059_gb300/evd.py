@@ -50,6 +50,11 @@ class evd_species(ctypes.Structure):
                 ("flags", ctypes.c_uint)]
 
 
+class evd_member(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("wall_mask", ctypes.c_uint), ("species", evd_species)]
+
+
 _lock = threading.Lock()
 _lib = None
 _vp, _dp, _st = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
@@ -83,6 +88,27 @@ _SIGNATURES = {
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
     "evd_destroy": (_st, [_vp]),
     "evd_last_error": (ctypes.c_char_p, [_vp]),
+    # include/evd_batch.h
+    "evd_batch_create": (_st, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(evd_member), ctypes.c_int, _vp,
+                               ctypes.POINTER(_vp)]),
+    "evd_batch_sizes": (_st, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "evd_batch_set_fields": (_st, [_vp, _vp, _vp]),
+    "evd_batch_step": (_st, [_vp, ctypes.c_longlong]),
+    "evd_batch_readout_device": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "evd_batch_get_mole_fractions": (_st, [_vp, _vp]),
+    "evd_batch_get_densities": (_st, [_vp, _vp]),
+    "evd_batch_get_velocities": (_st, [_vp, _vp, _vp]),
+    "evd_batch_get_species_mass": (_st, [_vp, _vp]),
+    "evd_batch_set_schedule": (_st, [_vp, ctypes.c_int, ctypes.c_int]),
+    "evd_batch_get_schedule": (_st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "evd_batch_autotune": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "evd_batch_set_graph": (_st, [_vp, ctypes.c_int]),
+    "evd_batch_set_mass_correction": (_st, [_vp, ctypes.c_int]),
+    "evd_batch_time": (ctypes.c_longlong, [_vp]),
+    "evd_batch_launch_count": (ctypes.c_longlong, [_vp]),
+    "evd_batch_check": (_st, [_vp]),
+    "evd_batch_destroy": (_st, [_vp]),
+    "evd_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 
@@ -111,6 +137,12 @@ def lib():
 def _check(status: int, ctx=None):
     if status != EVD_OK:
         msg = lib().evd_last_error(ctx)
+        raise EVDError(status, msg.decode() if msg else "")
+
+
+def _bcheck(status: int, batch=None):
+    if status != EVD_OK:
+        msg = lib().evd_batch_last_error(batch)
         raise EVDError(status, msg.decode() if msg else "")
 
 
@@ -282,6 +314,93 @@ def evd_last_error(ctx=None) -> str:
     return lib().evd_last_error(ctx).decode()
 
 
+# ------------------------------------------------ the batch (evd_batch.h)
+def evd_batch_create(lattice: int, precision: int, members, stream=None):
+    """members: a ctypes array of evd_member (keep the species arrays alive)."""
+    out = _vp()
+    _bcheck(lib().evd_batch_create(int(lattice), int(precision), members, len(members), _stream(stream),
+                                   ctypes.byref(out)))
+    return out
+
+
+def evd_batch_sizes(b) -> tuple[int, int]:
+    s, ss = ctypes.c_longlong(), ctypes.c_longlong()
+    _bcheck(lib().evd_batch_sizes(b, ctypes.byref(s), ctypes.byref(ss)), b)
+    return s.value, ss.value
+
+
+def evd_batch_set_fields(b, x, n=None):
+    _bcheck(lib().evd_batch_set_fields(b, _ptr(x), _ptr(n)), b)
+
+
+def evd_batch_step(b, nsteps: int):
+    _bcheck(lib().evd_batch_step(b, int(nsteps)), b)
+
+
+def evd_batch_readout_device(b, x=None, rho=None, u=None, ui=None):
+    _bcheck(lib().evd_batch_readout_device(b, _ptr(x), _ptr(rho), _ptr(u), _ptr(ui)), b)
+
+
+def evd_batch_get_mole_fractions(b, out):
+    _bcheck(lib().evd_batch_get_mole_fractions(b, _ptr(out, writable=True)), b)
+
+
+def evd_batch_get_densities(b, out):
+    _bcheck(lib().evd_batch_get_densities(b, _ptr(out, writable=True)), b)
+
+
+def evd_batch_get_velocities(b, u_out=None, ui_out=None):
+    _bcheck(lib().evd_batch_get_velocities(b, _ptr(u_out, writable=True), _ptr(ui_out, writable=True)), b)
+
+
+def evd_batch_get_species_mass(b, out):
+    _bcheck(lib().evd_batch_get_species_mass(b, _ptr(out, writable=True)), b)
+
+
+def evd_batch_set_schedule(b, item_sites: int, ctas_per_sm: int):
+    _bcheck(lib().evd_batch_set_schedule(b, int(item_sites), int(ctas_per_sm)), b)
+
+
+def evd_batch_get_schedule(b) -> tuple[int, int]:
+    i, c = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().evd_batch_get_schedule(b, ctypes.byref(i), ctypes.byref(c)), b)
+    return i.value, c.value
+
+
+def evd_batch_autotune(b, steps_per_trial: int = 8) -> tuple[int, int]:
+    i, c = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().evd_batch_autotune(b, int(steps_per_trial), ctypes.byref(i), ctypes.byref(c)), b)
+    return i.value, c.value
+
+
+def evd_batch_set_graph(b, steps_per_graph: int):
+    _bcheck(lib().evd_batch_set_graph(b, int(steps_per_graph)), b)
+
+
+def evd_batch_set_mass_correction(b, every: int):
+    _bcheck(lib().evd_batch_set_mass_correction(b, int(every)), b)
+
+
+def evd_batch_time(b) -> int:
+    return lib().evd_batch_time(b)
+
+
+def evd_batch_launch_count(b) -> int:
+    return lib().evd_batch_launch_count(b)
+
+
+def evd_batch_check(b):
+    _bcheck(lib().evd_batch_check(b), b)
+
+
+def evd_batch_destroy(b):
+    _bcheck(lib().evd_batch_destroy(b))
+
+
+def evd_batch_last_error(b=None) -> str:
+    return lib().evd_batch_last_error(b).decode()
+
+
 # ------------------------------------------------------- convenience layer
 class Simulation:
     """One EVD lattice on the current CUDA device (owns an evd_ctx).
@@ -362,3 +481,98 @@ class Simulation:
 
     def check(self):
         evd_check(self.ctx)
+
+
+class Batch:
+    """Many independent lattices of one lattice type and precision advanced
+    together (owns an evd_batch).  Members are given as seeded workloads (or
+    anything with lattice, shape, wall_mask, M, D, tau1, g); per-member
+    arrays are returned as lists in member order, site axes (nz, ny, nx)."""
+
+    def __init__(self, members, precision="fp32", stream=None):
+        members = list(members)
+        if not members:
+            raise ValueError("a batch needs at least one member")
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.lattice = int(members[0].lattice)
+        self.Q = 9 if self.lattice == EVD_D2Q9 else 19
+        self.D = 2 if self.lattice == EVD_D2Q9 else 3
+        self._tables = [SpeciesTable(m.M, m.D, m.tau1, m.g) for m in members]
+        arr = (evd_member * len(members))()
+        self.shapes, self.ns = [], []
+        for k, m in enumerate(members):
+            nx, ny, nz = (tuple(m.shape) + (1, 1))[:3]
+            arr[k] = evd_member(int(nx), int(ny), int(nz), int(m.wall_mask), self._tables[k].struct)
+            self.shapes.append((nz, ny, nx))
+            self.ns.append(len(self._tables[k].M))
+        self._members = arr
+        self.b = evd_batch_create(self.lattice, self.precision, arr, stream)
+        self.nsites, self.nspecies_sites = evd_batch_sizes(self.b)
+
+    @classmethod
+    def from_workloads(cls, workloads, precision="fp32", stream=None):
+        bt = cls(workloads, precision, stream)
+        bt.set_fields([w.x for w in workloads], [w.n for w in workloads])
+        return bt
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            evd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, xs, ns=None):
+        x = np.concatenate([np.ascontiguousarray(a, dtype=np.float64).ravel() for a in xs])
+        n = None
+        if ns is not None and any(a is not None for a in ns):
+            n = np.concatenate([np.ones(int(np.prod(s))) if a is None else
+                                np.ascontiguousarray(a, dtype=np.float64).ravel()
+                                for a, s in zip(ns, self.shapes)])
+        evd_batch_set_fields(self.b, x, n)
+
+    def step(self, nsteps=1):
+        evd_batch_step(self.b, nsteps)
+
+    @property
+    def t(self):
+        return evd_batch_time(self.b)
+
+    def _split(self, flat, per_site):
+        out, k = [], 0
+        for s, c in zip(self.shapes, per_site):
+            n = int(np.prod(s)) * c
+            out.append(flat[k:k + n].reshape((c,) + s))
+            k += n
+        return out
+
+    def mole_fractions(self):
+        out = np.empty(self.nspecies_sites)
+        evd_batch_get_mole_fractions(self.b, out)
+        return self._split(out, self.ns)
+
+    def densities(self):
+        out = np.empty(self.nspecies_sites)
+        evd_batch_get_densities(self.b, out)
+        return self._split(out, self.ns)
+
+    def velocities(self):
+        u = np.empty(self.D * self.nsites)
+        ui = np.empty(self.D * self.nspecies_sites)
+        evd_batch_get_velocities(self.b, u, ui)
+        us = self._split(u, [self.D] * len(self.ns))
+        uis = [a.reshape((n, self.D) + a.shape[1:]) for a, n in
+               zip(self._split(ui, [self.D * n for n in self.ns]), self.ns)]
+        return us, uis
+
+    def species_mass(self):
+        out = np.empty(len(self.ns) * EVD_MAX_SPECIES)
+        evd_batch_get_species_mass(self.b, out)
+        return [out[k * EVD_MAX_SPECIES:k * EVD_MAX_SPECIES + n] for k, n in enumerate(self.ns)]
+
+    def check(self):
+        evd_batch_check(self.b)

@@ -202,6 +202,46 @@ def random_mixture(lattice: int, shape: tuple, wall_mask: int, M: tuple,
                     tau1, gg, 0, x, nfield, seed)
 
 
+TUBE_BELOW = {2: (0.9, 0.1), 3: (0.7, 0.2, 0.1)}   # mole fractions in the lower half
+TUBE_ABOVE = {2: (0.1, 0.9), 3: (0.1, 0.2, 0.7)}   # and in the upper half
+
+
+def batched_tubes(count: int = 512, width: int = 32, lmin: int = 128, lmax: int = 4096,
+                  steps: int = 10000, seed: int = SEED, width_interface: float = 0.0) -> list:
+    """A sweep of independent D2Q9 Loschmidt tubes (periodic across the width,
+    impermeable ends): tube k draws, from stream 1000 + 4k, its length
+    L = lmin (lmax/lmin)^u log-uniform, 2 or 3 species (even odds), the mass
+    ratio M_max/M_min ~ U[1, 10] (M_min = 1, an intermediate mass uniform in
+    between), D_ij ~ U[0.01, 0.1] for two species and U[0.06, 0.1] for three
+    (stream 1001 + 4k) and gravity g ~ U[0, 5e-6] along -y.  Ternary tubes
+    with a mass ratio near 10 and D_ij below about 0.05 diverge within tens of
+    steps even in FP64 (the cross relaxation over-relaxes), hence their
+    narrower range.  Fill: a step profile at L/2 between the two compositions
+    of TUBE_BELOW / TUBE_ABOVE (an erf of half-width ``width_interface`` nodes
+    if it is > 0), number density 1."""
+    from math import erf
+    out = []
+    for k in range(count):
+        base = 1000 + 4 * k
+        u = uniform01(base, 5, seed)
+        L = int(round(lmin * (lmax / lmin) ** u[0]))
+        ns = 2 if u[1] < 0.5 else 3
+        r = 1.0 + 9.0 * u[2]
+        M = (1.0, r) if ns == 2 else (1.0, 1.0 + (r - 1.0) * u[3], r)
+        g = 5e-6 * u[4]
+        D = pair_diffusivities(ns, 0.01 if ns == 2 else 0.06, 0.1, base + 1, seed)
+        if width_interface > 0:
+            s = np.array([0.5 * (1.0 + erf((y + 0.5 - L / 2) / width_interface)) for y in range(L)])
+        else:
+            s = (np.arange(L) >= L // 2).astype(np.float64)
+        x = np.empty((ns, 1, L, width))
+        for i in range(ns):
+            x[i, 0, :, :] = (TUBE_BELOW[ns][i] * (1.0 - s) + TUBE_ABOVE[ns][i] * s)[:, None]
+        out.append(Workload(f"tube{k}-d2q9-{width}x{L}-ns{ns}", D2Q9, (width, L, 1), WALL_Y,
+                            M, D, 1.0, (0.0, -g, 0.0), steps, x, seed=seed))
+    return out
+
+
 def by_name(name: str) -> Workload:
     """The full-size workloads by short name."""
     table = {

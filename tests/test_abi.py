@@ -11,9 +11,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "evd.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(evd_\w+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(evd_\w+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(evd):
@@ -62,3 +66,26 @@ def test_null_context_calls_fail_cleanly(evd):
     assert L.evd_time(None) == -1
     assert L.evd_launch_count(None) == -1
     assert L.evd_set_mass_correction(None, 4) == evd.EVD_ERR_ARG
+
+
+def test_batch_rejects_invalid_members_before_any_cuda_call(evd):
+    good = evd.SpeciesTable([1.0, 2.0], np.full((2, 2), 0.05), 1.0)
+    bad = evd.SpeciesTable([2.0, 1.0], np.full((2, 2), 0.05), 1.0)   # decreasing masses
+    arr = (evd.evd_member * 2)(evd.evd_member(8, 8, 1, 0, good.struct), evd.evd_member(8, 8, 1, 0, bad.struct))
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_batch_create(evd.EVD_D2Q9, evd.EVD_FP32, arr)
+    assert ei.value.status == evd.EVD_ERR_ARG
+    assert "member 1" in evd.evd_batch_last_error(None)
+    with pytest.raises(evd.EVDError):
+        evd.evd_batch_create(evd.EVD_D2Q9, 7, arr)
+    with pytest.raises(evd.EVDError):
+        evd.evd_batch_create(evd.EVD_D2Q9, evd.EVD_FP32, (evd.evd_member * 0)())
+
+
+def test_null_batch_calls_fail_cleanly(evd):
+    L = evd.lib()
+    assert L.evd_batch_step(None, 1) == evd.EVD_ERR_ARG
+    assert L.evd_batch_check(None) == evd.EVD_ERR_ARG
+    assert L.evd_batch_set_schedule(None, 128, 0) == evd.EVD_ERR_ARG
+    assert L.evd_batch_time(None) == -1 and L.evd_batch_launch_count(None) == -1
+    assert L.evd_batch_destroy(None) == evd.EVD_OK

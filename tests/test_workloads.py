@@ -39,3 +39,29 @@ def test_paper_gases_fill_the_tube_halves():
     assert np.all(np.diff(wl.x[2, 0, 26:38, 0]) > 0)
     assert abs(wl.x[2, 0, 31, 0] + wl.x[2, 0, 32, 0] - (0.7 + 0.001)) < 0.02
     assert np.all((wl.D[np.triu_indices(3, 1)] >= 0.02) & (wl.D[np.triu_indices(3, 1)] <= 0.1))
+
+
+def test_batched_tube_sweep_draws_the_stated_ranges():
+    tubes = W.batched_tubes()
+    assert len(tubes) == 512
+    again = W.batched_tubes(count=3)
+    for a, b in zip(tubes[:3], again):
+        assert a.shape == b.shape and a.M == b.M and np.array_equal(a.D, b.D) and a.g == b.g
+    lengths = np.array([t.shape[1] for t in tubes])
+    assert lengths.min() >= 128 and lengths.max() <= 4096
+    # log-uniform: the median length is near sqrt(128 * 4096) = 724
+    assert 550 < np.median(lengths) < 950
+    ns = np.array([t.ns for t in tubes])
+    assert set(ns) == {2, 3} and 0.4 < (ns == 3).mean() < 0.6
+    for t in tubes:
+        assert t.shape[0] == 32 and t.shape[2] == 1 and t.wall_mask == W.WALL_Y
+        assert t.M[0] == 1.0 and list(t.M) == sorted(t.M) and t.M[-1] <= 10.0
+        off = t.D[np.triu_indices(t.ns, 1)]
+        assert off.min() >= (0.01 if t.ns == 2 else 0.06) and off.max() <= 0.1
+        assert t.g[0] == 0.0 and -5e-6 <= t.g[1] <= 0.0 and t.g[2] == 0.0
+        assert np.allclose(t.x.sum(axis=0), 1.0, atol=1e-15)
+        L = t.shape[1]
+        below, above = t.x[:, 0, L // 2 - 1, 0], t.x[:, 0, L // 2, 0]
+        assert np.allclose(below, W.TUBE_BELOW[t.ns]) and np.allclose(above, W.TUBE_ABOVE[t.ns])
+    # 19.3 M sites, 48.1 M species-site updates per step
+    assert 18e6 < sum(t.nsites for t in tubes) < 21e6
