@@ -280,8 +280,8 @@ def replica_throughput(ms_local: float, ssu_rank: int, device) -> tuple[float, f
     return ms_max, world * ssu_rank / (ms_max * 1e-3) / 1e9
 
 
-def tubes_config() -> dict:
-    return {"workload": "batched-tubes-d2q9-512x32", "lattice": "D2Q9", "members": 512, "width": 32,
+def tubes_config(members: int = 512) -> dict:
+    return {"workload": f"batched-tubes-d2q9-{members}x32", "lattice": "D2Q9", "members": members, "width": 32,
             "length": "log-uniform [128, 4096]", "species": "2 or 3", "mass_ratio": "U[1, 10]",
             "walls": ["y-", "y+"], "seed": W.SEED}
 
@@ -291,14 +291,18 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
     launch per step, replayed from CUDA graphs, schedule picked by the
     autotuner before the timed region."""
     from paper_2504_07059_gb300 import evd
-    tubes = W.batched_tubes()
+    tubes = W.batched_tubes()[:args.members]
     prec = args.precision
     stream = torch.cuda.current_stream(dev)
     b = evd.Batch(tubes, prec, stream)
     x_all = np.concatenate([t.x.ravel() for t in tubes])
     evd.evd_batch_set_fields(b.b, x_all)   # host path once, for the mass targets
     t0 = time.perf_counter()
-    sched = evd.evd_batch_autotune(b.b, 8)
+    if args.schedule:
+        sched = tuple(int(v) for v in args.schedule.split(","))
+        evd.evd_batch_set_schedule(b.b, *sched)
+    else:
+        sched = evd.evd_batch_autotune(b.b, 8)
     tune_s = time.perf_counter() - t0
     ssu_step = sum(t.ns * t.nsites for t in tubes)
     bpl = sum(t.ns * t.nsites * 2 * 9 * {"fp64": 8, "fp32": 4, "fp16": 2}[prec] for t in tubes)
@@ -369,8 +373,9 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)"}[prec],
             "data": "synthetic",
-            "config": dict(tubes_config(), precision=prec, parallelism=f"replicas{world}",
-                           schedule={"item_sites": sched[0], "ctas_per_sm": sched[1], "autotune_s": tune_s},
+            "config": dict(tubes_config(len(tubes)), precision=prec, parallelism=f"replicas{world}",
+                           schedule={"item_sites": sched[0], "ctas_per_sm": sched[1],
+                                     "autotune_s": None if args.schedule else tune_s},
                            graph_steps=8, l2="inputs larger than L2 (no flush needed)"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
@@ -544,6 +549,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 step for comparison")
+    ap.add_argument("--members", type=int, default=512, help="tubes workload: the first N tubes of the sweep")
+    ap.add_argument("--schedule", default="", help="tubes workload: 'item_sites,ctas_per_sm' instead of autotuning")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (2 or 4)")
     args = ap.parse_args()
     if args.warmup < 3:

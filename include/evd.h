@@ -204,7 +204,8 @@ evd_status evd_set_tile_rows(evd_ctx* ctx, int rows);
  * per-species mass of f_t in double precision; the deficit from the initial
  * masses (the target, computed in double at evd_set_fields) is re-injected in
  * the next step as f_a += w_a (m0_i - m_i)/sites at every node.  0 turns it
- * off.  Default: off for EVD_FP64, every 8 steps for EVD_FP32/EVD_FP16_STORE. */
+ * off.  Default: off for EVD_FP64, every 8 steps for EVD_FP32, every step for
+ * EVD_FP16_STORE (its storage rounding drifts the mass faster). */
 evd_status evd_set_mass_correction(evd_ctx* ctx, int every);
 
 /* The FP64 target masses [n_species] (initial species masses).  Synchronises. */

@@ -110,7 +110,8 @@ evd_status evd_batch_autotune(evd_batch* b, int steps_per_trial, int* item_sites
 evd_status evd_batch_set_graph(evd_batch* b, int steps_per_graph);
 
 /* FP64 species-mass correction of every member, as evd_set_mass_correction:
- * every `every` steps (0 = off; default off for EVD_FP64, 8 otherwise). */
+ * every `every` steps (0 = off; default off for EVD_FP64, 8 for EVD_FP32, 1
+ * for EVD_FP16_STORE). */
 evd_status evd_batch_set_mass_correction(evd_batch* b, int every);
 
 /* Steps taken since evd_batch_set_fields; -1 for NULL. */

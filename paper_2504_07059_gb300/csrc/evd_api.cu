@@ -568,7 +568,9 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
     c->corr[1] = (double*)((char*)c->small + part_bytes + 768);
     c->err_flag = (unsigned*)((char*)c->small + part_bytes + 1024);
     c->corr_pending = c->corr_applied = -1;
-    c->mc_every = (c->precision == EVD_FP64) ? 0 : 8;
+    // FP16 storage rounding moves the species mass by ~1e-7 per step on rough
+    // fields, so it is corrected every step; FP32 drifts ~1e-9 per step
+    c->mc_every = (c->precision == EVD_FP64) ? 0 : (c->precision == EVD_FP32 ? 8 : 1);
     e = cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) {
         evd_destroy(c);

@@ -447,7 +447,7 @@ evd_status evd_batch_create(int lattice, int precision, const evd_member* member
     b->buf_bytes = (size_t)foff * b->elem;
     b->tot_sites = soff;
     b->tot_ssites = xoff;
-    b->mc_every = precision == EVD_FP64 ? 0 : 8;
+    b->mc_every = precision == EVD_FP64 ? 0 : (precision == EVD_FP32 ? 8 : 1);
     b->corr_pending = b->corr_applied = -1;
     b->graph_steps = 8;
     cudaError_t e = cudaGetDevice(&b->device);
