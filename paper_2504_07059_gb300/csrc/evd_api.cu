@@ -157,10 +157,18 @@ long long plane_stride(const evd_grid* g)
     return (n + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
 }
 
+// Planes of a population buffer: one per (species, direction), plus one per
+// species holding the node densities that half storage decodes with.
+int buffer_planes(int lattice, int precision, int ns)
+{
+    const int Q = lattice == EVD_D2Q9 ? 9 : 19;
+    return ns * Q + (precision == EVD_FP16_STORE ? ns : 0);
+}
+
 size_t buffer_bytes(const evd_grid* g, const evd_species* s)
 {
-    const int Q = g->lattice == EVD_D2Q9 ? 9 : 19;
-    return (size_t)plane_stride(g) * (size_t)(s->n_species * Q) * elem_size(g->precision);
+    return (size_t)plane_stride(g) * (size_t)buffer_planes(g->lattice, g->precision, s->n_species) *
+           elem_size(g->precision);
 }
 
 // Constants of the scheme for this run (double precision).
@@ -238,16 +246,19 @@ void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
 namespace {
 
 using evd::buffer_bytes;
+using evd::buffer_planes;
 using evd::elem_size;
 using evd::fill_params;
 using evd::plane_stride;
 using evd::validate;
 
+// Global deviation references of float storage (half storage keeps one per
+// node instead; FP64 stores populations as they are).
 void set_reference(evd_ctx* c, const double* rho_ref)
 {
     for (int i = 0; i < MAXS; ++i)
         for (int k = 0; k < 3; ++k)
-            c->hp.ref[i][k] = (c->precision == EVD_FP64 || i >= c->ns) ? 0.0 : c->hp.wl[k] * rho_ref[i];
+            c->hp.ref[i][k] = (c->precision != EVD_FP32 || i >= c->ns) ? 0.0 : c->hp.wl[k] * rho_ref[i];
 }
 
 cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, const double* corr)
@@ -468,7 +479,8 @@ bool tma_setup(evd_ctx* c)
     if (c->lattice != EVD_D3Q19 || c->precision == EVD_FP64) return false;
     if (!c->hp.wall[0] || !c->hp.wall[1]) return false;
     if (c->nx < 2 || c->ny < 2 || (c->hp.wall[2] && c->nz < 2)) return false;
-    if ((long long)c->ns * 19 * c->pstride >= (1LL << 31)) return false;
+    const int planes = buffer_planes(c->lattice, c->precision, c->ns);
+    if ((long long)planes * c->pstride >= (1LL << 31)) return false;
     const size_t elem = c->elem;
     if (((size_t)c->nx * elem) % 16 != 0) return false;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -482,15 +494,17 @@ bool tma_setup(evd_ctx* c)
     }
     const int TY = c->tma_ty, TX = evd::TmaLaunch::TX;
     const int XP = (int)(16 / elem);
-    // storage groups: halo class (bit 0 x, bit 1 y) and number of directions
-    const int gcls[7] = {0, 0, 1, 1, 2, 2, 3};
-    const int gsize[7] = {1, 2, 2, 4, 2, 4, 4};
-    const cuuint64_t dims[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)(c->ns * 19)};
+    // storage groups: halo class (bit 0 x, bit 1 y) and planes per species;
+    // group 7 is the node densities of half storage (planes ns * 19 + i)
+    const int gcls[8] = {0, 0, 1, 1, 2, 2, 3, 3};
+    const int gsize[8] = {1, 2, 2, 4, 2, 4, 4, 1};
+    const int ngroups = c->precision == EVD_FP16_STORE ? 8 : 7;
+    const cuuint64_t dims[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)planes};
     const cuuint64_t strides[3] = {(cuuint64_t)c->nx * elem, (cuuint64_t)c->nx * c->ny * elem,
                                    (cuuint64_t)c->pstride * elem};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int b = 0; b < 2; ++b)
-        for (int g = 0; g < 7; ++g) {
+        for (int g = 0; g < ngroups; ++g) {
             const int cls = gcls[g];
             const cuuint32_t box[4] = {(cuuint32_t)((cls & 1) ? TX + 2 * XP : TX),
                                        (cuuint32_t)((cls & 2) ? TY + 2 : TY), 1,

@@ -439,7 +439,7 @@ evd_status evd_batch_create(int lattice, int precision, const evd_member* member
         mi.uoff = soff * b->D;
         mi.uioff = xoff * b->D;
         for (int i = 0; i < mi.ns; ++i) mi.M[i] = mb.species.molar_mass[i];
-        foff += (long long)mi.ns * b->Q * b->hp[m].pstride;
+        foff += (long long)evd::buffer_planes(lattice, precision, mi.ns) * b->hp[m].pstride;
         xoff += (long long)mi.ns * mi.sites;
         soff += mi.sites;
     }
@@ -526,7 +526,8 @@ evd_status evd_batch_set_fields(evd_batch* b, const double* x, const double* n)
             HostParams& h = b->hp[k];
             for (int i = 0; i < MAXS; ++i)
                 for (int c = 0; c < 3; ++c)
-                    h.ref[i][c] = i < h.ns ? h.wl[c] * m[(size_t)k * MAXS + i] / h.nsites : 0.0;
+                    h.ref[i][c] = (i < h.ns && b->precision == EVD_FP32) ? h.wl[c] * m[(size_t)k * MAXS + i] / h.nsites
+                                                                         : 0.0;
         }
         s = upload_params(b);
         if (s != EVD_OK) return s;

@@ -63,7 +63,7 @@ __device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__
         if (corr) add_correction<LAT, NS>(p, corr, f);
         moments<LAT, NS>(p, f, s, err);
         collide<LAT, NS>(p, f, s);
-        store_all<LAT, NS>(p, fout, node, f);
+        store_all<LAT, NS>(p, fout, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
     }
@@ -192,10 +192,10 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
                 f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
             });
         });
-        store_all<LAT, NS>(p, fprev, node, f);
         moments<LAT, NS>(p, f, s, err);
+        store_all<LAT, NS>(p, fprev, node, f, s.rho);
         collide<LAT, NS>(p, f, s);
-        store_all<LAT, NS>(p, fcur, node, f);
+        store_all<LAT, NS>(p, fcur, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
     }

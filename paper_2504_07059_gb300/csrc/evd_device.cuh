@@ -109,6 +109,14 @@ __host__ __device__ constexpr int plane_of(int i, int a)
                     : NS * grp_start(grp<LAT>(a)) + i * grp_size(grp<LAT>(a)) + grp_pos<LAT>(a);
 }
 
+// Plane of the stored node densities rho~_i of species i (half storage):
+// after the NS * Q population planes.
+template <int LAT, int NS>
+__host__ __device__ constexpr int ref_plane(int i)
+{
+    return NS * Lat<LAT>::Q + i;
+}
+
 // --------------------------------------------------------------- parameters
 // Per-run constants, computed on the host in double and cast to T.
 template <typename T>
@@ -157,22 +165,31 @@ inline Params<T> to_params(const HostParams& h)
 }
 
 // --------------------------------------------------------- storage codecs
-// Raw double storage, or the deviation f - w_a rho_ref_i in float / half.
+// Raw double storage; float storage of the deviation f - w_a rho_ref_i from
+// one reference density per species; half storage of the deviation
+// f - w_a rho~_i(x) from the node's own density rho~_i(x), which is stored
+// (as a half, so exactly) in one extra plane per species.  A stored value at
+// node X decodes with the reference of X itself.
 template <typename S> struct Codec;
 template <> struct Codec<double> {
     static constexpr bool DEV = false;
+    static constexpr bool LOCAL = false;
     static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <> struct Codec<float> {
     static constexpr bool DEV = true;
+    static constexpr bool LOCAL = false;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <> struct Codec<__half> {
     static constexpr bool DEV = true;
+    static constexpr bool LOCAL = true;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    // the value a float takes once stored
+    static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
 
 // ------------------------------------------------------------- neighbours
@@ -221,12 +238,20 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
 {
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
     const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
+    const S* rplane = fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node;
+    const T wa = p.wl[wclass<LAT>(A)];
+    // the stored value at offset o, decoded with that node's own reference
+    // where the storage keeps one per node
+    auto ldv = [&](long long o) -> T {
+        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(plane + o));
+        else return (T)Codec<S>::ld(plane + o);
+    };
     T acc;
     if constexpr (ex == 0 && ey == 0 && ez == 0) {
-        acc = (T)Codec<S>::ld(plane);
+        acc = ldv(0);
     } else {
         if (p.unit[I]) {
-            acc = (T)Codec<S>::ld(plane + nb.off[0][1 - ex] + nb.off[1][1 - ey] + nb.off[2][1 - ez]);
+            acc = ldv(nb.off[0][1 - ex] + nb.off[1][1 - ey] + nb.off[2][1 - ez]);
         } else {
             constexpr int k1 = ex != 0 ? 0 : (ey != 0 ? 1 : 2);
             constexpr int k2 = (ex != 0 && ey != 0) ? 1 : (((ex != 0 || ey != 0) && ez != 0) ? 2 : -1);
@@ -235,15 +260,14 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
             if constexpr (k2 < 0) {
 #pragma unroll
                 for (int o1 = -1; o1 <= 1; ++o1)
-                    acc += p.w1[I][widx(o1, e1)] * (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1]);
+                    acc += p.w1[I][widx(o1, e1)] * ldv(nb.off[k1][o1 + 1]);
             } else if constexpr (std::is_same<T, double>::value) {
                 constexpr int e2 = ev<LAT>(A, k2);
 #pragma unroll
                 for (int o2 = -1; o2 <= 1; ++o2)
 #pragma unroll
                     for (int o1 = -1; o1 <= 1; ++o1)
-                        acc += p.w2[I][widx(o1, e1)][widx(o2, e2)] *
-                               (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
+                        acc += p.w2[I][widx(o1, e1)][widx(o2, e2)] * ldv(nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
             } else {
                 // float arithmetic: two 1-D passes, so that the effective 2-D
                 // weights are products of 1-D weights that sum to exactly one
@@ -253,14 +277,13 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
                     T row = (T)0;
 #pragma unroll
                     for (int o1 = -1; o1 <= 1; ++o1)
-                        row += p.w1[I][widx(o1, e1)] *
-                               (T)Codec<S>::ld(plane + nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
+                        row += p.w1[I][widx(o1, e1)] * ldv(nb.off[k1][o1 + 1] + nb.off[k2][o2 + 1]);
                     acc += p.w1[I][widx(o2, e2)] * row;
                 }
             }
         }
     }
-    if constexpr (Codec<S>::DEV) acc += p.ref[I][wclass<LAT>(A)];
+    if constexpr (Codec<S>::DEV && !Codec<S>::LOCAL) acc += p.ref[I][wclass<LAT>(A)];
     return acc;
 }
 
@@ -318,7 +341,14 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
     constexpr int AB = opp<LAT>(A);
     const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
-    const T ref = Codec<S>::DEV ? p.ref[I][wclass<LAT>(A)] : (T)0;
+    const S* rplane = fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node;
+    const T wa = p.wl[wclass<LAT>(A)];
+    const T ref = (Codec<S>::DEV && !Codec<S>::LOCAL) ? p.ref[I][wclass<LAT>(A)] : (T)0;
+    // stored value of plane q at offset o, decoded (node reference if kept)
+    auto ldv = [&](const S* q, long long o) -> T {
+        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(q + o));
+        else return (T)Codec<S>::ld(q + o);
+    };
     T acc = (T)0;
 #pragma unroll
     for (int oz = (ez ? -1 : 0); oz <= (ez ? 1 : 0); ++oz)
@@ -331,16 +361,14 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
                                    (oz == -1 && nb.lo[2]) || (oz == 1 && nb.hi[2]);
                 if (!solid) {
                     const T w = push_weight<LAT, A>(p, I, -ox, -oy, -oz);  // from O + o to O: d = -o
-                    acc += w * ((T)Codec<S>::ld(plane + nb.off[0][ox + 1] + nb.off[1][oy + 1] +
-                                                nb.off[2][oz + 1]) + ref);
+                    acc += w * (ldv(plane, nb.off[0][ox + 1] + nb.off[1][oy + 1] + nb.off[2][oz + 1]) + ref);
                 }
             }
     if constexpr (ex != 0 || ey != 0 || ez != 0) {
         const T ls = lumped<LAT, A>(p, I, nb, true);
         const T lo = lumped<LAT, AB>(p, I, nb, false);
-        if (ls != (T)0) acc += ls * ((T)Codec<S>::ld(plane) + ref);
-        if (lo != (T)0)
-            acc += lo * ((T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node) + ref);
+        if (ls != (T)0) acc += ls * (ldv(plane, 0) + ref);
+        if (lo != (T)0) acc += lo * (ldv(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node, 0) + ref);
     }
     return acc;
 }
@@ -379,23 +407,34 @@ __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             T v = (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
-            if constexpr (Codec<S>::DEV) v += p.ref[I][wclass<LAT>(A)];
+            if constexpr (Codec<S>::LOCAL)
+                v = fma(p.wl[wclass<LAT>(A)], (T)Codec<S>::ld(fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node), v);
+            else if constexpr (Codec<S>::DEV)
+                v += p.ref[I][wclass<LAT>(A)];
             f[I][A] = v;
         });
     });
 }
 
+// rho: the node's species densities, the references of half storage (stored
+// rounded to half, and the deviations taken from that rounded value).
 template <int LAT, int NS, typename S, typename T>
 __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fout, int node,
-                                          const T (&f)[NS][Lat<LAT>::Q])
+                                          const T (&f)[NS][Lat<LAT>::Q], const T (&rho)[NS])
 {
     constexpr int Q = Lat<LAT>::Q;
     static_for<0, NS>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
+        T rr = (T)0;
+        if constexpr (Codec<S>::LOCAL) {
+            rr = (T)Codec<S>::rt((float)rho[I]);
+            Codec<S>::st(fout + (long long)ref_plane<LAT, NS>(I) * p.pstride + node, (float)rr);
+        }
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             T v = f[I][A];
-            if constexpr (Codec<S>::DEV) v -= p.ref[I][wclass<LAT>(A)];
+            if constexpr (Codec<S>::LOCAL) v -= p.wl[wclass<LAT>(A)] * rr;
+            else if constexpr (Codec<S>::DEV) v -= p.ref[I][wclass<LAT>(A)];
             Codec<S>::st(fout + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node, v);
         });
     });
@@ -615,7 +654,7 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
         if (corr) add_correction<LAT, NS>(p, corr, f);
         moments<LAT, NS>(p, f, s, err);
         collide<LAT, NS>(p, f, s);
-        store_all<LAT, NS>(p, fout, node, f);
+        store_all<LAT, NS>(p, fout, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }
     if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
@@ -703,10 +742,10 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
                 });
             });
         }
-        store_all<LAT, NS>(p, fprev, node, f);
         moments<LAT, NS>(p, f, s, err);
+        store_all<LAT, NS>(p, fprev, node, f, s.rho);
         collide<LAT, NS>(p, f, s);
-        store_all<LAT, NS>(p, fcur, node, f);
+        store_all<LAT, NS>(p, fcur, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }
     block_mass<NS>(s.rho, active, mass_part);

@@ -39,6 +39,7 @@ struct HostParams {
 size_t elem_size(int precision);
 bool validate(const evd_grid* g, const evd_species* s, std::string& msg);
 long long plane_stride(const evd_grid* g);
+int buffer_planes(int lattice, int precision, int ns);
 size_t buffer_bytes(const evd_grid* g, const evd_species* s);
 void fill_params(HostParams& h, const evd_grid* g, const evd_species* s);
 
@@ -98,7 +99,7 @@ inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + bloc
 // maps points to the seven tensor maps (CUtensorMap, 128 bytes each) of the
 // input buffer, one per storage group of directions.
 struct TmaLaunch {
-    static constexpr int TX = 32, SLOTS = 4, NGROUPS = 7;
+    static constexpr int TX = 32, SLOTS = 4, NGROUPS = 8;   // at most 8 tensor maps per buffer
     // rows per tile: 4 (one CTA per SM) or 2 (two CTAs per SM)
     static int zchunk(const HostParams& h) { return h.nz < 32 ? h.nz : 32; }
     static int grid(const HostParams& h, int ty)

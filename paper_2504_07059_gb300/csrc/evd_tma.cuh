@@ -42,26 +42,37 @@
 namespace evd {
 
 constexpr int TTX = 32;
-constexpr int NGRP = 7;
+constexpr int NGRP = 7;       // storage groups of directions
+constexpr int NGRP_MAX = 8;   // + the node-density planes of half storage (group 7)
 constexpr unsigned ERR_TIMEOUT = 4u;
 
 template <typename S> struct TmaPad;
 template <> struct TmaPad<float> { static constexpr int XP = 4; };   // 16 bytes
 template <> struct TmaPad<__half> { static constexpr int XP = 8; };  // 16 bytes
 
-// halo class of a storage group: bit 0 moves in x, bit 1 moves in y
-__host__ __device__ constexpr int grp_cls(int g) { return g == 2 || g == 3 ? 1 : g == 4 || g == 5 ? 2 : g == 6 ? 3 : 0; }
+// halo class of a storage group: bit 0 moves in x, bit 1 moves in y (the
+// node densities, group 7, are read at every in-plane stencil node)
+__host__ __device__ constexpr int grp_cls(int g)
+{
+    return g == 2 || g == 3 ? 1 : g == 4 || g == 5 ? 2 : g == 6 || g == 7 ? 3 : 0;
+}
 __host__ __device__ constexpr bool grp_moves_z(int g) { return g == 1 || g == 3 || g == 5; }
+// loaded for the halo z-planes too: the z-moving groups, and the node
+// densities that decode them
+__host__ __device__ constexpr bool grp_on_halo(int g) { return grp_moves_z(g) || g == 7; }
+__host__ __device__ constexpr int grp_planes(int g) { return g == 7 ? 1 : grp_size(g); }
 
 template <int NS, typename S, int TY, int SLOTS>
 struct TmaLayout {
     static constexpr int XP = TmaPad<S>::XP;
+    static constexpr bool LOCAL = Codec<S>::LOCAL;
+    static constexpr int NG = LOCAL ? NGRP + 1 : NGRP;
     static __host__ __device__ constexpr int bw(int cls) { return (cls & 1) ? TTX + 2 * XP : TTX; }
     static __host__ __device__ constexpr int bh(int cls) { return (cls & 2) ? TY + 2 : TY; }
     static __host__ __device__ constexpr int plane_elems(int g) { return bw(grp_cls(g)) * bh(grp_cls(g)); }
     static __host__ __device__ constexpr int box_bytes(int g)
     {
-        return plane_elems(g) * NS * grp_size(g) * (int)sizeof(S);
+        return plane_elems(g) * NS * grp_planes(g) * (int)sizeof(S);
     }
     static __host__ __device__ constexpr int group_offset(int g)
     {
@@ -69,12 +80,12 @@ struct TmaLayout {
         for (int q = 0; q < g; ++q) o += (box_bytes(q) + 127) / 128 * 128;
         return o;
     }
-    static constexpr int slot_bytes = group_offset(NGRP);
-    static __host__ __device__ constexpr int stage_bytes(bool zonly)
+    static constexpr int slot_bytes = group_offset(NG);
+    static __host__ __device__ constexpr int stage_bytes(bool halo)
     {
         int s = 0;
-        for (int g = 0; g < NGRP; ++g)
-            if (!zonly || grp_moves_z(g)) s += box_bytes(g);
+        for (int g = 0; g < NG; ++g)
+            if (!halo || grp_on_halo(g)) s += box_bytes(g);
         return s;
     }
     static constexpr int ring_bytes = SLOTS * slot_bytes;
@@ -135,11 +146,11 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 struct TmaMaps {
-    CUtensorMap m[NGRP];   // one per storage group of the input buffer
+    CUtensorMap m[NGRP_MAX];   // one per storage group of the input buffer
 };
 
 // Which z-planes a stage loads: all groups for z in [zb, ze), only the
-// z-moving groups for the halo planes zb-1 and ze.
+// z-moving groups (and node densities) for the halo planes zb-1 and ze.
 __device__ __forceinline__ bool stage_is_halo(int k, int zb, int ze) { return k < zb || k >= ze; }
 
 // masked 1-D weights of one in-plane dimension for a direction component e
@@ -168,11 +179,13 @@ __device__ __forceinline__ MaskedW masked_weights(const float (&w)[3], bool lo, 
     return m;
 }
 
-// In-plane interpolation of direction A (decoded: includes the deviation
-// reference scaled by the weight the fluid stencil nodes carry).
+// In-plane interpolation of direction A, decoded: float storage adds its
+// reference ref scaled by the weight the fluid stencil nodes carry; half
+// storage decodes every stencil value with the density rho~ stored for that
+// node (group 7 of the stage), scaled by the lattice weight wa.
 template <int A, int NS, typename S, int TY, int SLOTS>
 __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int tx, int ty, const MaskedW& mx,
-                                         const MaskedW& my, float ref)
+                                         const MaskedW& my, float ref, float wa)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
@@ -184,15 +197,27 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
                  (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
     const int cx = tx + ((cls & 1) ? G::XP : 0);
     const int cy = ty + ((cls & 2) ? 1 : 0);
-    auto ld = [&](int yy, int xx) -> float { return (float)s[yy * W + xx]; };
+    auto ld = [&](int yy, int xx) -> float {
+        if constexpr (G::LOCAL) {
+            // the density tile has the x and y halo; shift into its frame
+            constexpr int W7 = G::bw(3), DX = (cls & 1) ? 0 : G::XP, DY = (cls & 2) ? 0 : 1;
+            const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
+            return fmaf(wa, (float)r[(yy + DY) * W7 + xx + DX], (float)s[yy * W + xx]);
+        } else {
+            return (float)s[yy * W + xx];
+        }
+    };
     if constexpr (cls == 0) {
-        return ld(cy, cx) + ref;
+        if constexpr (G::LOCAL) return ld(cy, cx);
+        else return ld(cy, cx) + ref;
     } else if constexpr (cls == 1) {
-        return mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1) +
-               ref * mx.sum[xi];
+        const float v = mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1);
+        if constexpr (G::LOCAL) return v;
+        else return v + ref * mx.sum[xi];
     } else if constexpr (cls == 2) {
-        return my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx) +
-               ref * my.sum[yi];
+        const float v = my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx);
+        if constexpr (G::LOCAL) return v;
+        else return v + ref * my.sum[yi];
     } else {
         float acc = 0.0f;
 #pragma unroll
@@ -201,13 +226,14 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
                               mx.w[xi][2] * ld(cy + oy, cx + 1);
             acc += my.w[yi][oy + 1] * row;
         }
-        return acc + ref * mx.sum[xi] * my.sum[yi];
+        if constexpr (G::LOCAL) return acc;
+        else return acc + ref * mx.sum[xi] * my.sum[yi];
     }
 }
 
 // Unit lattice speed off the walls: weights (1, 0, 0), the upstream node.
 template <int A, int NS, typename S, int TY, int SLOTS>
-__device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float ref)
+__device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float ref, float wa)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
@@ -218,7 +244,13 @@ __device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp,
                  (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
     const int cx = tx + ((cls & 1) ? G::XP : 0) - ex;
     const int cy = ty + ((cls & 2) ? 1 : 0) - ey;
-    return (float)s[cy * W + cx] + ref;
+    if constexpr (G::LOCAL) {
+        constexpr int W7 = G::bw(3), DX = (cls & 1) ? 0 : G::XP, DY = (cls & 2) ? 0 : 1;
+        const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
+        return fmaf(wa, (float)r[(cy + DY) * W7 + cx + DX], (float)s[cy * W + cx]);
+    } else {
+        return (float)s[cy * W + cx] + ref;
+    }
 }
 
 template <int NS, typename S, int TY, int SLOTS>
@@ -254,14 +286,14 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     __syncthreads();
 
     // copy parameters of the storage group this lane of warp 0 issues
-    const int g = lane < NGRP ? lane : 0;
+    const int g = lane < G::NG ? lane : 0;
     const int gcls = grp_cls(g);
     const int gcx = (gcls & 1) ? x0 - G::XP : x0;
     const int gcy = (gcls & 2) ? y0 - 1 : y0;
-    const int gc3 = NS * grp_start(g);
+    const int gc3 = g == 7 ? NS * 19 : NS * grp_start(g);   // group 7: the node densities
     const unsigned goff = (unsigned)G::group_offset(g);
-    const bool gz = grp_moves_z(g);
-    const bool issuer = warp == 0 && lane < NGRP;
+    const bool gz = grp_on_halo(g);
+    const bool issuer = warp == 0 && lane < G::NG;
     auto issue = [&](int idx) {
         const int slot = idx % SLOTS;
         const int k = kfirst + idx;
@@ -291,7 +323,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     const MaskedW mx = masked_weights(w, xlo, xhi), my = masked_weights(w, ylo, yhi);
     const bool unit_fast = p.unit[sp] && !col_wall;
     const int nxy = p.nx * p.ny;
-    const int pstride = (int)p.pstride;   // the host guarantees NS * 19 * pstride < 2^31
+    const int pstride = (int)p.pstride;   // the host guarantees planes * pstride < 2^31
     const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
 
     // running sums: z-moving directions (A: node at z = k-1, B: node at k),
@@ -319,42 +351,44 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
         const int node = x + p.nx * y + nxy * zo;
         const bool wall_node = emit && active && (col_wall || zlo || zhi);
-        float f[Q], cen[Q];
+        float f[Q], cen[Q], cenr = 0.0f;
         if (wall_node) {
             // the node's own post-collision populations, for the App. A terms
             static_for<1, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 cen[A] = (float)fin[plane_of<1, NS>(sp, A) * pstride + node];
             });
+            if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
         }
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
         if (ok && unit_fast) {
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = ref_c[wclass<1>(A)];
+                const float ref = ref_c[wclass<1>(A)], wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
-                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
                 } else if constexpr (ez > 0) {
                     // exact shift: node z takes slab z - 1, which arrived two iterations ago
                     f[A] = accA[A];
                     accA[A] = accB[A];
-                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
                 } else {
-                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref);
+                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
                 }
             });
         } else if (ok) {
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = ref_c[wclass<1>(A)];
+                const float ref = ref_c[wclass<1>(A)], wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
-                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref);
+                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref, wa);
                 } else {
-                    const float R = solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref);
+                    const float R =
+                        solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref, wa);
                     // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
                     f[A] = accA[A] + w[widx(1, ez)] * R;
                     accA[A] = accB[A] + w[widx(0, ez)] * R;
@@ -371,9 +405,14 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                 static_for<1, Q>([&](auto ac) {
                     constexpr int A = decltype(ac)::value;
                     constexpr int AB = opp<1>(A);
-                    const float ref = ref_c[wclass<1>(A)];
                     const float2 l = __ldg(L + A);
-                    f[A] += l.x * (cen[A] + ref) + l.y * (cen[AB] + ref);
+                    if constexpr (G::LOCAL) {
+                        const float wa = p.wl[wclass<1>(A)];
+                        f[A] += l.x * fmaf(wa, cenr, cen[A]) + l.y * fmaf(wa, cenr, cen[AB]);
+                    } else {
+                        const float ref = ref_c[wclass<1>(A)];
+                        f[A] += l.x * (cen[A] + ref) + l.y * (cen[AB] + ref);
+                    }
                 });
             }
             if (corr) {
@@ -477,6 +516,12 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const float wr[3] = {p.wl[0] * rho, p.wl[1] * rho, p.wl[2] * rho};
         const float sr = rho * inv_cs2 * sfac;
         if (active) mass_acc += (double)rho;
+        // half storage: the node density, rounded as stored, is the reference
+        float rr = 0.0f;
+        if constexpr (G::LOCAL) {
+            rr = Codec<S>::rt(rho);
+            if (active) Codec<S>::st(fout + (ref_plane<1, NS>(sp) * pstride + node), rr);
+        }
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             constexpr int C = wclass<1>(A);
@@ -488,8 +533,10 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             const float B = fmaf(c_inv_cs2, ea, Bc);
             const float S_ = p.wl[C] * sr * fmaf(csp * eg, 1.0f + t1, -ug);
             const float fs = fmaf(omt, f[A], fmaf(feq, B, S_));
-            if (active)
-                Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - ref_c[C]);
+            if (active) {
+                if constexpr (G::LOCAL) Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - p.wl[C] * rr);
+                else Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - ref_c[C]);
+            }
         });
     }
 

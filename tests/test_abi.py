@@ -35,8 +35,9 @@ def test_version_and_required_bytes(evd):
     g = evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP32, (64, 1024), evd.EVD_WALL_YM | evd.EVD_WALL_YP)
     assert evd.evd_required_bytes(g, sp) == 64 * 1024 * 27 * 4
     g3 = evd.make_grid(evd.EVD_D3Q19, evd.EVD_FP16_STORE, (5, 7, 3), 0)
-    # planes padded to 64 elements: 105 sites -> 128
-    assert evd.evd_required_bytes(g3, sp) == 128 * 57 * 2
+    # planes padded to 64 elements: 105 sites -> 128; half storage keeps one
+    # node-density plane per species besides the 57 population planes
+    assert evd.evd_required_bytes(g3, sp) == 128 * (57 + 3) * 2
 
 
 @pytest.mark.parametrize("bad", [
