@@ -82,7 +82,8 @@ def bytes_per_ssu(wl: W.Workload, precision: str) -> int:
     """Algorithmic HBM bytes per species-site update: each population read
     once and written once (ping-pong)."""
     elem = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
-    return 2 * wl.Q * elem
+    # half storage also reads and writes the node's stored density
+    return 2 * wl.Q * elem + (2 * elem if precision == "fp16" else 0)
 
 
 class ClockSampler:
@@ -305,7 +306,7 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
         sched = evd.evd_batch_autotune(b.b, 8)
     tune_s = time.perf_counter() - t0
     ssu_step = sum(t.ns * t.nsites for t in tubes)
-    bpl = sum(t.ns * t.nsites * 2 * 9 * {"fp64": 8, "fp32": 4, "fp16": 2}[prec] for t in tubes)
+    bpl = sum(t.ns * t.nsites * bytes_per_ssu(t, prec) for t in tubes)
     evd.evd_batch_step(b.b, args.warmup)
     torch.cuda.synchronize(dev)
     if world > 1:

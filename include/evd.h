@@ -66,7 +66,12 @@ typedef enum { EVD_D2Q9 = 0, EVD_D3Q19 = 1 } evd_lattice;
  *   EVD_FP64       double storage, double arithmetic.
  *   EVD_FP32       float storage of the deviation f - w_a rho_ref_i, float
  *                  arithmetic (rho_ref_i = mean initial density of species i).
- *   EVD_FP16_STORE half storage of the same deviation, float arithmetic.
+ *   EVD_FP16_STORE half storage of the deviation f - w_a rho~_i(x) from the
+ *                  node's own species density, which is stored too (as a
+ *                  half, one extra plane per species); float arithmetic.
+ *                  Each stored value decodes with the density stored at its
+ *                  own node, so interpolation still conserves mass and the
+ *                  deviations stay small where densities differ strongly.
  * Per-species mass reductions are double in every mode. */
 typedef enum { EVD_FP64 = 0, EVD_FP32 = 1, EVD_FP16_STORE = 2 } evd_precision;
 

@@ -76,12 +76,6 @@ def test_reduced_precision_members_match_the_oracle(evd, precision):
     b = batch_run(evd, members, steps, precision)
     xs, ms = b.mole_fractions(), b.species_mass()
     for k, m in enumerate(members):
-        if precision == "fp16" and m.name.startswith("loschmidt-binary"):
-            # FP16 deviations from one global reference density cannot follow
-            # the 9:1 density contrast of the binary tube (x within 1e-3, mass
-            # within 1e-6); the single-lattice parity test keeps this case as a
-            # strict xfail
-            continue
         m0 = np.array([(m.x[i] * m.M[i] * (1.0 if m.n is None else m.n)).sum() for i in range(m.ns)])
         assert max_rel(ms[k], m0) < TOL_MASS[precision], k
         o = oracle_run(m, steps)

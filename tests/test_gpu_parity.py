@@ -62,11 +62,6 @@ def test_fp64_time_zero_readout_is_the_initial_state(evd):
 REDUCED = [(n, p) for n in ["d2q9-binary-tube-4x256", "d2q9-ternary-ragged-walls-y",
                              "d2q9-ternary-box-corners", "d3q19-ternary-closed-box",
                              "d3q19-stratification-32"] for p in ("fp32", "fp16")]
-# FP16 deviations from a single reference density per species cannot follow
-# the 9:1 density contrast of the binary tube for 2000 steps within 1e-3.
-REDUCED = [pytest.param(n, p, marks=pytest.mark.xfail(strict=True, reason="FP16 storage with a global "
-                                                      "reference density; contrast too large"))
-           if (n, p) == ("d2q9-binary-tube-4x256", "fp16") else (n, p) for n, p in REDUCED]
 
 
 @pytest.mark.parametrize("name,precision", REDUCED)
