@@ -453,9 +453,13 @@ double lump_weight(const HostParams& h, int i, int b, const bool lo[3], const bo
 }
 
 // Table [27 wall classes][ns][19] of (L_self, L_opp) floats for the TMA step.
+// Per (wall class, species, direction): the App. A lumped weights L_self,
+// L_opp, and K - 1 where K is the sum of every weight feeding that population
+// (the fluid stencil weights and both lumps); float storage, which gathers
+// deviations from a reference, adds the reference times K - 1.
 bool build_lumps(evd_ctx* c)
 {
-    const int n = 27 * c->ns * 19 * 2;
+    const int n = 27 * c->ns * 19 * 4;
     float* host = new float[n];
     for (int cls = 0; cls < 27; ++cls) {
         const int cc[3] = {cls % 3, (cls / 3) % 3, cls / 9};
@@ -463,9 +467,24 @@ bool build_lumps(evd_ctx* c)
         for (int k = 0; k < 3; ++k) { lo[k] = cc[k] == 1; hi[k] = cc[k] == 2; }
         for (int i = 0; i < c->ns; ++i)
             for (int a = 0; a < 19; ++a) {
-                float* t = host + ((cls * c->ns + i) * 19 + a) * 2;
-                t[0] = a ? (float)lump_weight(c->hp, i, a, lo, hi, true) : 0.0f;
-                t[1] = a ? (float)lump_weight(c->hp, i, opp19(a), lo, hi, false) : 0.0f;
+                float* t = host + ((cls * c->ns + i) * 19 + a) * 4;
+                const double ls = a ? lump_weight(c->hp, i, a, lo, hi, true) : 0.0;
+                const double lop = a ? lump_weight(c->hp, i, opp19(a), lo, hi, false) : 0.0;
+                double kin = 1.0;   // fluid stencil weights: product of masked 1-D sums
+                for (int k = 0; k < 3; ++k) {
+                    const int e = kE19[a][k];
+                    if (e == 0) continue;
+                    double sk = 0.0;
+                    for (int o = -1; o <= 1; ++o) {
+                        if ((o == -1 && lo[k]) || (o == 1 && hi[k])) continue;
+                        sk += c->hp.w1[i][o == -e ? 0 : (o == 0 ? 1 : 2)];
+                    }
+                    kin *= sk;
+                }
+                t[0] = (float)ls;
+                t[1] = (float)lop;
+                t[2] = (float)(kin + ls + lop - 1.0);
+                t[3] = 0.0f;
             }
     }
     bool ok = cudaMalloc((void**)&c->lumps, n * sizeof(float)) == cudaSuccess &&

@@ -61,8 +61,8 @@ __device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__
         const Nbr nb = neighbours(p, node);
         gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS>(p, f, s, err);
-        collide<LAT, NS>(p, f, s);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
@@ -122,7 +122,7 @@ __device__ __noinline__ void item_readout(const Params<T>& p, const MemberInfo& 
             gather_all<LAT, NS>(p, fin, node, nb, f);
             if (corr) add_correction<LAT, NS>(p, corr, f);
         }
-        moments<LAT, NS>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             if (x) x[mi.xoff + i * n + node] = (double)(s.rho[i] * p.Minv[i]) / (double)s.n;
@@ -192,9 +192,17 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
                 f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
             });
         });
-        moments<LAT, NS>(p, f, s, err);
+        if constexpr (Codec<S>::DARITH)   // float storage computes on deviations
+            static_for<0, NS>([&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int A = decltype(ac)::value;
+                    f[I][A] -= p.ref[I][wclass<LAT>(A)];
+                });
+            });
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
         store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS>(p, f, s);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
         store_all<LAT, NS>(p, fcur, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];

@@ -140,6 +140,9 @@ struct Params {
     T w2[MAXS][3][3];      // products w1[a] * w1[b]
     T wl[3];               // lattice weight per class (rest, axis, diagonal)
     T ref[MAXS][3];        // deviation reference per class: wl[class] * rho_ref_i
+    // float storage computes in deviations g = f - ref (see Codec::DARITH):
+    T rref[MAXS];          // sum over directions of ref: the density g = 0 stands for
+    T refc[MAXS][3];       // wl[class] * rref - ref[class], the rounding of ref, exactly
 };
 
 template <typename T>
@@ -161,6 +164,13 @@ inline Params<T> to_params(const HostParams& h)
             for (int b = 0; b < 3; ++b) p.w2[i][a][b] = (T)h.w2[i][a][b];
         }
     }
+    // directions per class: rest, axis, diagonal
+    const double n1 = h.lattice == 0 ? 4.0 : 6.0, n2 = h.lattice == 0 ? 4.0 : 12.0;
+    for (int i = 0; i < MAXS; ++i) {
+        const double r0 = (double)p.ref[i][0], r1 = (double)p.ref[i][1], r2 = (double)p.ref[i][2];
+        p.rref[i] = (T)(r0 + n1 * r1 + n2 * r2);
+        for (int a = 0; a < 3; ++a) p.refc[i][a] = (T)((double)p.wl[a] * (double)p.rref[i] - (double)p.ref[i][a]);
+    }
     return p;
 }
 
@@ -174,18 +184,25 @@ template <typename S> struct Codec;
 template <> struct Codec<double> {
     static constexpr bool DEV = false;
     static constexpr bool LOCAL = false;
+    static constexpr bool DARITH = false;
     static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <> struct Codec<float> {
     static constexpr bool DEV = true;
     static constexpr bool LOCAL = false;
+    // arithmetic on the deviations g = f - ref themselves: the gather, the
+    // moments (rho = rref + sum g, j = sum e g) and the collision never form
+    // the full-size populations, whose float rounding would swamp the small
+    // momenta and forcing terms of near-rest mixtures
+    static constexpr bool DARITH = true;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <> struct Codec<__half> {
     static constexpr bool DEV = true;
     static constexpr bool LOCAL = true;
+    static constexpr bool DARITH = false;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
     // the value a float takes once stored
@@ -283,7 +300,8 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
             }
         }
     }
-    if constexpr (Codec<S>::DEV && !Codec<S>::LOCAL) acc += p.ref[I][wclass<LAT>(A)];
+    // float storage: acc is the deviation g = f - ref itself (the weights sum
+    // to exactly one); half storage decoded every value; FP64 is raw
     return acc;
 }
 
@@ -343,7 +361,11 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
     const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
     const S* rplane = fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node;
     const T wa = p.wl[wclass<LAT>(A)];
-    const T ref = (Codec<S>::DEV && !Codec<S>::LOCAL) ? p.ref[I][wclass<LAT>(A)] : (T)0;
+    // float storage gathers deviations; the reference carried by the weights
+    // of this node, ref * (K - 1) with K the sum of the fluid stencil weights
+    // and the lumped ones, is added at the end (K = 1 away from walls)
+    const T ref = (T)0;
+    T ksum = (T)0;
     // stored value of plane q at offset o, decoded (node reference if kept)
     auto ldv = [&](const S* q, long long o) -> T {
         if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(q + o));
@@ -362,6 +384,7 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
                 if (!solid) {
                     const T w = push_weight<LAT, A>(p, I, -ox, -oy, -oz);  // from O + o to O: d = -o
                     acc += w * (ldv(plane, nb.off[0][ox + 1] + nb.off[1][oy + 1] + nb.off[2][oz + 1]) + ref);
+                    ksum += w;
                 }
             }
     if constexpr (ex != 0 || ey != 0 || ez != 0) {
@@ -369,7 +392,9 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
         const T lo = lumped<LAT, AB>(p, I, nb, false);
         if (ls != (T)0) acc += ls * (ldv(plane, 0) + ref);
         if (lo != (T)0) acc += lo * (ldv(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node, 0) + ref);
+        ksum += ls + lo;
     }
+    if constexpr (Codec<S>::DARITH) acc += p.ref[I][wclass<LAT>(A)] * (ksum - (T)1);
     return acc;
 }
 
@@ -409,9 +434,7 @@ __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict
             T v = (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
             if constexpr (Codec<S>::LOCAL)
                 v = fma(p.wl[wclass<LAT>(A)], (T)Codec<S>::ld(fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node), v);
-            else if constexpr (Codec<S>::DEV)
-                v += p.ref[I][wclass<LAT>(A)];
-            f[I][A] = v;
+            f[I][A] = v;   // float storage: the deviation itself
         });
     });
 }
@@ -425,7 +448,7 @@ __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fo
     constexpr int Q = Lat<LAT>::Q;
     static_for<0, NS>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        T rr = (T)0;
+        [[maybe_unused]] T rr = (T)0;
         if constexpr (Codec<S>::LOCAL) {
             rr = (T)Codec<S>::rt((float)rho[I]);
             Codec<S>::st(fout + (long long)ref_plane<LAT, NS>(I) * p.pstride + node, (float)rr);
@@ -433,8 +456,7 @@ __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fo
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             T v = f[I][A];
-            if constexpr (Codec<S>::LOCAL) v -= p.wl[wclass<LAT>(A)] * rr;
-            else if constexpr (Codec<S>::DEV) v -= p.ref[I][wclass<LAT>(A)];
+            if constexpr (Codec<S>::LOCAL) v -= p.wl[wclass<LAT>(A)] * rr;   // float: already a deviation
             Codec<S>::st(fout + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node, v);
         });
     });
@@ -461,6 +483,7 @@ struct NodeState {
     T ueq[NS][3];
     T u[3];
     T V[NS][3];   // sum_j (rho_j / rho) (u_i^eq - u_j^eq) / tau_ij = Theta_i / rho_i
+    T drho[NS];   // sum_a g_a: rho_i - rref_i (deviation arithmetic)
     T rho_mix, n;
 };
 
@@ -469,7 +492,9 @@ struct NodeState {
 // the cross relaxation rates 1/tau_ij of Eq. (relation_tauij_diff_coeff):
 // Eq. (Luo&Girimaji_tau) for two species and the Sec. 4.1 closed forms for
 // three, written for 1/tau_ij.
-template <int LAT, int NS, typename T>
+// DA: f holds deviations g = f - ref (float storage): rho_i = rref_i + sum g,
+// j_i = sum e g (the references cancel in j).
+template <int LAT, int NS, bool DA = false, typename T>
 __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat<LAT>::Q],
                                         NodeState<NS, T>& s, unsigned& err)
 {
@@ -490,6 +515,8 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
             if constexpr (ev<LAT>(A, 2) == 1) j[2] += v;
             if constexpr (ev<LAT>(A, 2) == -1) j[2] -= v;
         });
+        s.drho[I] = r;
+        if constexpr (DA) r = p.rref[I] + r;
         if (!(r > (T)0)) err |= ERR_RHO;
         const T rinv = (T)1 / r;
         s.rho[I] = r;
@@ -555,14 +582,19 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 //      S = w [e/c_s^2 + (ee - c_s^2 I).u/c_s^4].F_i (Eq. CE_forcing_term_discretized),
 // rearranged to  f* = (1 - 1/tau) f + f^eq [1/tau + (e-u).a/c_s^2] + (1-1/(2tau)) S,
 //                a  = (u_i^eq - u)/tau - V_i.
-template <int LAT, int NS, typename T>
+// DA: f holds deviations g = f - ref and receives g* = f* - ref, written so
+// that every term is small:
+//   g* = (1 - 1/tau) g + (w drho + refc)/tau + w rho (phi B + b) + (1 - 1/(2 tau)) S
+// with feq = w rho (1 + phi), phi = t1 (1 + t1/2) - u^2/(2 c_s^2),
+//      B = 1/tau + b, b = (e-u).a / c_s^2 (the same algebra as above, minus ref).
+template <int LAT, int NS, bool DA = false, typename T>
 __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
                                         const NodeState<NS, T>& s)
 {
     constexpr int Q = Lat<LAT>::Q;
     const T usq = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
     const T ug = s.u[0] * p.g[0] + s.u[1] * p.g[1] + s.u[2] * p.g[2];
-    T av[NS][3], Bc[NS], U2[NS], wr[NS][3], sr[NS];
+    T av[NS][3], Bc[NS], U2[NS], wr[NS][3], sr[NS], Bm[NS], dt[NS][3];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         T ua = (T)0;
@@ -572,9 +604,13 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
             ua += s.u[k] * av[i][k];
         }
         Bc[i] = p.tau_inv[i] - p.inv_cs2[i] * ua;
-        U2[i] = (T)1 - (T)0.5 * p.inv_cs2[i] * usq;
+        Bm[i] = -p.inv_cs2[i] * ua;
+        U2[i] = DA ? -(T)0.5 * p.inv_cs2[i] * usq : (T)1 - (T)0.5 * p.inv_cs2[i] * usq;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) wr[i][c] = p.wl[c] * s.rho[i];
+        for (int c = 0; c < 3; ++c) {
+            wr[i][c] = p.wl[c] * s.rho[i];
+            if constexpr (DA) dt[i][c] = p.tau_inv[i] * fma(p.wl[c], s.drho[i], p.refc[i][c]);
+        }
         sr[i] = s.rho[i] * p.inv_cs2[i] * p.sfac[i];
     }
     static_for<0, Q>([&](auto ac) {
@@ -586,10 +622,17 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
         for (int i = 0; i < NS; ++i) {
             const T ea = edot<LAT, A>(av[i]);
             const T t1 = p.c_inv_cs2[i] * eu;                       // e.u / c_s^2
-            const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
-            const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);
             const T S = p.wl[C] * sr[i] * fma(p.c[i] * eg, (T)1 + t1, -ug);
-            f[i][A] = fma(p.omt[i], f[i][A], fma(feq, B, S));
+            if constexpr (DA) {
+                const T phi = fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
+                const T b = fma(p.c_inv_cs2[i], ea, Bm[i]);
+                const T B = p.tau_inv[i] + b;
+                f[i][A] = fma(p.omt[i], f[i][A], fma(wr[i][C], fma(phi, B, b), dt[i][C] + S));
+            } else {
+                const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
+                const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);
+                f[i][A] = fma(p.omt[i], f[i][A], fma(feq, B, S));
+            }
         }
     });
 }
@@ -652,8 +695,8 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
         const Nbr nb = neighbours(p, node);
         gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS>(p, f, s, err);
-        collide<LAT, NS>(p, f, s);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }
@@ -683,7 +726,7 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
             gather_all<LAT, NS>(p, fin, node, nb, f);
             if (corr) add_correction<LAT, NS>(p, corr, f);   // as the last step saw f_t
         }
-        moments<LAT, NS>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
         const long long ns_ = p.nsites;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -700,7 +743,11 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
 #pragma unroll
             for (int i = 0; i < NS; ++i)
 #pragma unroll
-                for (int a = 0; a < Q; ++a) fpop[(i * Q + a) * ns_ + node] = (double)f[i][a];
+                for (int a = 0; a < Q; ++a) {
+                    double v = (double)f[i][a];
+                    if constexpr (Codec<S>::DARITH) v += (double)p.ref[i][wclass<LAT>(a)];
+                    fpop[(i * Q + a) * ns_ + node] = v;
+                }
         }
         if (err) atomicOr(err_flag, err);
     }
@@ -742,9 +789,17 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
                 });
             });
         }
-        moments<LAT, NS>(p, f, s, err);
+        if constexpr (Codec<S>::DARITH)   // float storage computes on deviations
+            static_for<0, NS>([&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int A = decltype(ac)::value;
+                    f[I][A] -= p.ref[I][wclass<LAT>(A)];
+                });
+            });
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
         store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS>(p, f, s);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
         store_all<LAT, NS>(p, fcur, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }

@@ -109,8 +109,8 @@ struct TmaLaunch {
     }
 };
 
-// lumps: App. A coefficients [27 wall classes][ns][19] x (L_self, L_opp) as
-// float pairs; wall class = cx + 3 cy + 9 cz with c = 0 interior, 1 at the
+// lumps: App. A coefficients [27 wall classes][ns][19] x (L_self, L_opp,
+// K - 1, 0) as float4; wall class = cx + 3 cy + 9 cz with c = 0 interior, 1 at the
 // low wall, 2 at the high wall of that dimension.
 template <int PREC>
 cudaError_t launch_step_tma(const HostParams& h, int ty, const void* maps, const void* fin, void* fout,

@@ -179,10 +179,11 @@ __device__ __forceinline__ MaskedW masked_weights(const float (&w)[3], bool lo, 
     return m;
 }
 
-// In-plane interpolation of direction A, decoded: float storage adds its
-// reference ref scaled by the weight the fluid stencil nodes carry; half
-// storage decodes every stencil value with the density rho~ stored for that
-// node (group 7 of the stage), scaled by the lattice weight wa.
+// In-plane interpolation of direction A: float storage interpolates the
+// deviations from its reference as they are (the reference carried by the
+// weights is added at wall nodes only, through K - 1); half storage decodes
+// every stencil value with the density rho~ stored for that node (group 7 of
+// the stage), scaled by the lattice weight wa.
 template <int A, int NS, typename S, int TY, int SLOTS>
 __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int tx, int ty, const MaskedW& mx,
                                          const MaskedW& my, float ref, float wa)
@@ -207,17 +208,16 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
             return (float)s[yy * W + xx];
         }
     };
+    // float storage computes on deviations, half storage decoded each value:
+    // neither adds a reference here (ref is unused)
     if constexpr (cls == 0) {
-        if constexpr (G::LOCAL) return ld(cy, cx);
-        else return ld(cy, cx) + ref;
+        return ld(cy, cx);
     } else if constexpr (cls == 1) {
         const float v = mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1);
-        if constexpr (G::LOCAL) return v;
-        else return v + ref * mx.sum[xi];
+        return v;
     } else if constexpr (cls == 2) {
         const float v = my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx);
-        if constexpr (G::LOCAL) return v;
-        else return v + ref * my.sum[yi];
+        return v;
     } else {
         float acc = 0.0f;
 #pragma unroll
@@ -226,8 +226,7 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
                               mx.w[xi][2] * ld(cy + oy, cx + 1);
             acc += my.w[yi][oy + 1] * row;
         }
-        if constexpr (G::LOCAL) return acc;
-        else return acc + ref * mx.sum[xi] * my.sum[yi];
+        return acc;
     }
 }
 
@@ -249,7 +248,7 @@ __device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp,
         const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
         return fmaf(wa, (float)r[(cy + DY) * W7 + cx + DX], (float)s[cy * W + cx]);
     } else {
-        return (float)s[cy * W + cx] + ref;
+        return (float)s[cy * W + cx];
     }
 }
 
@@ -257,7 +256,7 @@ template <int NS, typename S, int TY, int SLOTS>
 __global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
-           const double* __restrict__ corr, const float2* __restrict__ lumps, int ntx, int nty, int zchunk)
+           const double* __restrict__ corr, const float4* __restrict__ lumps, int ntx, int nty, int zchunk)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int Q = 19;
@@ -314,7 +313,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     float w[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) w[a] = p.w1[sp][a];
-    const float ref_c[3] = {p.ref[sp][0], p.ref[sp][1], p.ref[sp][2]};
     const float csp = p.c[sp], inv_cs2 = p.inv_cs2[sp], c_inv_cs2 = p.c_inv_cs2[sp];
     const float tau_inv = p.tau_inv[sp], omt = p.omt[sp], sfac = p.sfac[sp];
     const bool xlo = p.wall[0] && x == 0, xhi = p.wall[0] && x == p.nx - 1;
@@ -365,7 +363,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = ref_c[wclass<1>(A)], wa = p.wl[wclass<1>(A)];
+                const float ref = 0.0f, wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
                     if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
@@ -382,7 +380,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = ref_c[wclass<1>(A)], wa = p.wl[wclass<1>(A)];
+                const float ref = 0.0f, wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
                     if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref, wa);
@@ -398,20 +396,19 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         }
 
         // ---- node (x, y, zo): wall terms, correction, moments
-        float rho = 1.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
+        float rho = 1.0f, drho = 0.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
         if (ok && emit) {
             if (wall_node) {
-                const float2* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
+                const float4* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
                 static_for<1, Q>([&](auto ac) {
                     constexpr int A = decltype(ac)::value;
                     constexpr int AB = opp<1>(A);
-                    const float2 l = __ldg(L + A);
+                    const float4 l = __ldg(L + A);
                     if constexpr (G::LOCAL) {
                         const float wa = p.wl[wclass<1>(A)];
                         f[A] += l.x * fmaf(wa, cenr, cen[A]) + l.y * fmaf(wa, cenr, cen[AB]);
-                    } else {
-                        const float ref = ref_c[wclass<1>(A)];
-                        f[A] += l.x * (cen[A] + ref) + l.y * (cen[AB] + ref);
+                    } else {   // deviations, plus the reference the weights carry
+                        f[A] += l.x * cen[A] + l.y * cen[AB] + p.ref[sp][wclass<1>(A)] * l.z;
                     }
                 });
             }
@@ -433,6 +430,8 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                 if constexpr (ev<1>(A, 2) == 1) j[2] += f[A];
                 if constexpr (ev<1>(A, 2) == -1) j[2] -= f[A];
             });
+            drho = r;
+            if constexpr (Codec<S>::DARITH) r = p.rref[sp] + r;
             if (active && !(r > 0.0f)) err |= ERR_RHO;
             rho = r;
             const float rinv = __fdividef(1.0f, r);
@@ -511,8 +510,14 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             av[d] = (ueq[d] - u[d]) * tau_inv - V[d];
             ua += u[d] * av[d];
         }
+        constexpr bool DA = Codec<S>::DARITH;   // float: the deviation form of the general kernel
         const float Bc = tau_inv - inv_cs2 * ua;
-        const float U2 = 1.0f - 0.5f * inv_cs2 * usq;
+        const float Bm = -inv_cs2 * ua;
+        const float U2 = DA ? -0.5f * inv_cs2 * usq : 1.0f - 0.5f * inv_cs2 * usq;
+        float dt[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (DA)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dt[c] = tau_inv * fmaf(p.wl[c], drho, p.refc[sp][c]);
         const float wr[3] = {p.wl[0] * rho, p.wl[1] * rho, p.wl[2] * rho};
         const float sr = rho * inv_cs2 * sfac;
         if (active) mass_acc += (double)rho;
@@ -529,13 +534,20 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             const float eg = edot<1, A>(p.g);
             const float ea = edot<1, A>(av);
             const float t1 = c_inv_cs2 * eu;
-            const float feq = wr[C] * fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
-            const float B = fmaf(c_inv_cs2, ea, Bc);
             const float S_ = p.wl[C] * sr * fmaf(csp * eg, 1.0f + t1, -ug);
-            const float fs = fmaf(omt, f[A], fmaf(feq, B, S_));
+            float fs;
+            if constexpr (DA) {   // g* directly: every term small
+                const float phi = fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
+                const float b = fmaf(c_inv_cs2, ea, Bm);
+                fs = fmaf(omt, f[A], fmaf(wr[C], fmaf(phi, tau_inv + b, b), dt[C] + S_));
+            } else {
+                const float feq = wr[C] * fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
+                const float B = fmaf(c_inv_cs2, ea, Bc);
+                fs = fmaf(omt, f[A], fmaf(feq, B, S_));
+            }
             if (active) {
                 if constexpr (G::LOCAL) Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - p.wl[C] * rr);
-                else Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - ref_c[C]);
+                else Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs);
             }
         });
     }

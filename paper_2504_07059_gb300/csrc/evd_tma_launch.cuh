@@ -19,7 +19,7 @@ cudaError_t launch_tma_ns(const HostParams& h, const TmaMaps& maps, const void* 
     const int ntx = (h.nx + TTX - 1) / TTX, nty = (h.ny + TY - 1) / TY;
     const dim3 block(L::threads);
     kern<<<TmaLaunch::grid(h, TY), block, L::total_bytes, st>>>(maps, p, (const S*)fin, (S*)fout, mp, err, flags,
-                                                            corr, (const float2*)lumps, ntx, nty,
+                                                            corr, (const float4*)lumps, ntx, nty,
                                                             TmaLaunch::zchunk(h));
     return cudaGetLastError();
 }
