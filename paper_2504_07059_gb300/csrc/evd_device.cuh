@@ -583,8 +583,9 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 // rearranged to  f* = (1 - 1/tau) f + f^eq [1/tau + (e-u).a/c_s^2] + (1-1/(2tau)) S,
 //                a  = (u_i^eq - u)/tau - V_i.
 // DA: f holds deviations g = f - ref and receives g* = f* - ref, written so
-// that every term is small:
-//   g* = (1 - 1/tau) g + (w drho + refc)/tau + w rho (phi B + b) + (1 - 1/(2 tau)) S
+// that only the last addition is at the size of g:
+//   g* = g + (w drho + refc - g)/tau + w rho (phi B + b) + (1 - 1/(2 tau)) S
+// (1 - 1/tau = omt exactly on the float grid of the constants)
 // with feq = w rho (1 + phi), phi = t1 (1 + t1/2) - u^2/(2 c_s^2),
 //      B = 1/tau + b, b = (e-u).a / c_s^2 (the same algebra as above, minus ref).
 template <int LAT, int NS, bool DA = false, typename T>
@@ -609,7 +610,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             wr[i][c] = p.wl[c] * s.rho[i];
-            if constexpr (DA) dt[i][c] = p.tau_inv[i] * fma(p.wl[c], s.drho[i], p.refc[i][c]);
+            if constexpr (DA) dt[i][c] = fma(p.wl[c], s.drho[i], p.refc[i][c]);   // w rho - ref
         }
         sr[i] = s.rho[i] * p.inv_cs2[i] * p.sfac[i];
     }
@@ -627,7 +628,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
                 const T phi = fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T b = fma(p.c_inv_cs2[i], ea, Bm[i]);
                 const T B = p.tau_inv[i] + b;
-                f[i][A] = fma(p.omt[i], f[i][A], fma(wr[i][C], fma(phi, B, b), dt[i][C] + S));
+                f[i][A] += fma(p.tau_inv[i], dt[i][C] - f[i][A], fma(wr[i][C], fma(phi, B, b), S));
             } else {
                 const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);

@@ -452,6 +452,13 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             const float4 v = exch[((idx & 1) * NS * TY + i * TY + ty) * TTX + tx];
             r[i] = v.x; ue[i][0] = v.y; ue[i][1] = v.z; ue[i][2] = v.w;
         }
+        // this thread's own rho and u^eq come back from the exchange (the same
+        // values), so that they need not stay in registers across the barrier
+        rho = r[0];
+        ueq[0] = ue[0][0]; ueq[1] = ue[0][1]; ueq[2] = ue[0][2];
+#pragma unroll
+        for (int i = 1; i < NS; ++i)
+            if (i == sp) { rho = r[i]; ueq[0] = ue[i][0]; ueq[1] = ue[i][1]; ueq[2] = ue[i][2]; }
         float rho_m = 0.0f, n = 0.0f;
 #pragma unroll
         for (int i = 0; i < NS; ++i) { rho_m += r[i]; n += r[i] * p.Minv[i]; }
@@ -517,7 +524,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float dt[3] = {0.0f, 0.0f, 0.0f};
         if constexpr (DA)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dt[c] = tau_inv * fmaf(p.wl[c], drho, p.refc[sp][c]);
+            for (int c = 0; c < 3; ++c) dt[c] = fmaf(p.wl[c], drho, p.refc[sp][c]);   // w rho - ref
         const float wr[3] = {p.wl[0] * rho, p.wl[1] * rho, p.wl[2] * rho};
         const float sr = rho * inv_cs2 * sfac;
         if (active) mass_acc += (double)rho;
@@ -539,7 +546,8 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             if constexpr (DA) {   // g* directly: every term small
                 const float phi = fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
                 const float b = fmaf(c_inv_cs2, ea, Bm);
-                fs = fmaf(omt, f[A], fmaf(wr[C], fmaf(phi, tau_inv + b, b), dt[C] + S_));
+                // g* = g + (w rho - ref - g)/tau + w rho (phi B + b) + S: one large addition
+                fs = f[A] + fmaf(tau_inv, dt[C] - f[A], fmaf(wr[C], fmaf(phi, tau_inv + b, b), S_));
             } else {
                 const float feq = wr[C] * fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
                 const float B = fmaf(c_inv_cs2, ea, Bc);
