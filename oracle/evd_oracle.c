@@ -64,6 +64,7 @@ typedef struct {
     int opp[OR_MAXQ];
     double c[OR_MAXS], cs2[OR_MAXS], tau[OR_MAXS];
     double *f, *fs, *fn;  /* [ns][Q][nsites] */
+    double* acc;          /* [3][nsites] per-node specific force added to g, or NULL */
     long t;
 } or_state;
 
@@ -251,6 +252,15 @@ int or_tau_cross(const or_config* cfg, const double* rho, double* tau_out)
     }
 }
 
+/* Specific body force at node X: the uniform g of the configuration plus
+ * the node's entry of the force field, when one is set (Sec. 4.2, Case II:
+ * F_i(r) = rho_i omega^2 r is such a field). */
+static void node_force(const or_state* st, long X, double a[3])
+{
+    int k;
+    for (k = 0; k < 3; ++k) a[k] = st->cfg.g[k] + (st->acc ? st->acc[(long)k * st->nsites + X] : 0.0);
+}
+
 /* -------------------------------------------------------------- collision
  * One node, all species, term by term in the paper's notation:
  *   moments: Eq. (zeroth_order_moment), Eq. (first_order_moment_force),
@@ -264,7 +274,7 @@ int or_tau_cross(const or_config* cfg, const double* rho, double* tau_out)
  *                                     + (1 - dt/(2 tau_i)) S^i
  * f and fstar are [ns][Q] for this node.  Returns 0 on a non-positive density.
  */
-static int collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg)
+static int collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg, const double* acc)
 {
     const or_config* cfg = &st->cfg;
     const int ns = cfg->ns, Q = st->Q;
@@ -283,7 +293,7 @@ static int collide_node(const or_state* st, const double* f, double* fstar, or_d
         }
         if (!(rho[i] > 0.0)) return 0;
         for (k = 0; k < 3; ++k) {
-            F[i][k] = rho[i] * cfg->g[k];
+            F[i][k] = rho[i] * acc[k];   /* F_i = rho_i (g + k(x)) */
             ueq[i][k] = mom[k] / rho[i] + F[i][k] * dt / (2.0 * rho[i]);
         }
         rho_mix += rho[i];
@@ -455,7 +465,24 @@ or_state* or_create(const or_config* cfg)
 void or_destroy(or_state* st)
 {
     if (!st) return;
-    free(st->f); free(st->fs); free(st->fn); free(st);
+    free(st->f); free(st->fs); free(st->fn); free(st->acc); free(st);
+}
+
+/* Per-node specific force field k(x), [3][nsites] (x fastest inside each
+ * component), added to the uniform g: F_i(x) = rho_i (g + k(x)).  NULL
+ * removes it.  Set it before or_init, whose initial velocities use it.
+ * Returns 0 if memory runs out. */
+int or_set_force_field(or_state* st, const double* k)
+{
+    if (!k) {
+        free(st->acc);
+        st->acc = NULL;
+        return 1;
+    }
+    if (!st->acc) st->acc = (double*)malloc(sizeof(double) * 3 * (size_t)st->nsites);
+    if (!st->acc) return 0;
+    memcpy(st->acc, k, sizeof(double) * 3 * (size_t)st->nsites);
+    return 1;
 }
 
 void or_species_info(const or_state* st, double* c, double* cs2, double* tau)
@@ -480,9 +507,10 @@ int or_init(or_state* st, const double* x, const double* nfield)
         const double n = nfield ? nfield[X] : 1.0;
         for (i = 0; i < ns; ++i) {
             const double rho_i = x[(long)i * nsites + X] * cfg->M[i] * n;
-            double ui0[3];
+            double ui0[3], a0[3];
             if (!(rho_i > 0.0)) return 0;
-            for (k = 0; k < 3; ++k) ui0[k] = 0.0 - rho_i * cfg->g[k] * dt / (2.0 * rho_i);
+            node_force(st, X, a0);
+            for (k = 0; k < 3; ++k) ui0[k] = 0.0 - rho_i * a0[k] * dt / (2.0 * rho_i);
             for (a = 0; a < Q; ++a) {
                 /* u = 0: f^{eq} = w rho_i; f^{(0)} = [1 + e.(u_i0 - 0)/cs2] f^{eq} */
                 double eu0 = 0.0;
@@ -518,7 +546,11 @@ static int collide_all(or_state* st)
     for (X = 0; X < nsites; ++X) {
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) fn[i * Q + a] = st->f[((long)i * Q + a) * nsites + X];
-        if (!collide_node(st, fn, fo, NULL)) return 0;
+        {
+            double acc[3];
+            node_force(st, X, acc);
+            if (!collide_node(st, fn, fo, NULL, acc)) return 0;
+        }
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) st->fs[((long)i * Q + a) * nsites + X] = fo[i * Q + a];
     }
@@ -560,7 +592,7 @@ int or_collide_only(or_state* st)
 /* One node through the collision, with every intermediate term returned. */
 int or_collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg)
 {
-    return collide_node(st, f, fstar, dg);
+    return collide_node(st, f, fstar, dg, st->cfg.g);
 }
 
 int or_diag_size(void) { return (int)sizeof(or_diag); }
@@ -582,7 +614,11 @@ int or_observables(const or_state* st, double* x, double* rho, double* u, double
     for (X = 0; X < nsites; ++X) {
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) fn[i * Q + a] = st->f[((long)i * Q + a) * nsites + X];
-        if (!collide_node(st, fn, fo, &dg)) return 0;
+        {
+            double acc[3];
+            node_force(st, X, acc);
+            if (!collide_node(st, fn, fo, &dg, acc)) return 0;
+        }
         for (i = 0; i < ns; ++i) {
             if (x) x[(long)i * nsites + X] = dg.rho[i] / (dg.n * st->cfg.M[i]);
             if (rho) rho[(long)i * nsites + X] = dg.rho[i];

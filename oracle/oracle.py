@@ -88,6 +88,8 @@ def lib():
             L.or_destroy.argtypes = [ctypes.c_void_p]
             L.or_init.restype = ctypes.c_int
             L.or_init.argtypes = [ctypes.c_void_p, dp, dp]
+            L.or_set_force_field.restype = ctypes.c_int
+            L.or_set_force_field.argtypes = [ctypes.c_void_p, dp]
             L.or_step.restype = ctypes.c_long
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
             L.or_stream_only.argtypes = [ctypes.c_void_p]
@@ -199,6 +201,16 @@ class Oracle:
         nn = None if n is None else np.ascontiguousarray(n, dtype=np.float64).reshape(self.nsites)
         if not lib().or_init(self._h, _dp(x), _dp(nn)):
             raise ValueError("oracle init: non-positive density")
+
+    def set_force_field(self, k):
+        """Per-node specific force k(x) added to g, shape (3, nz, ny, nx) or
+        (3, nsites); None removes it.  Set it before init (Sec. 4.2, Case II)."""
+        if k is None:
+            lib().or_set_force_field(self._h, None)
+            return
+        k = np.ascontiguousarray(k, dtype=np.float64).reshape(3, self.nsites)
+        if not lib().or_set_force_field(self._h, _dp(k)):
+            raise MemoryError("oracle force field")
 
     def step(self, nsteps=1):
         done = lib().or_step(self._h, int(nsteps))

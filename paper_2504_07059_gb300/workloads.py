@@ -73,6 +73,7 @@ class Workload:
     x: np.ndarray = field(repr=False)   # [ns][nz][ny][nx]
     n: np.ndarray | None = field(default=None, repr=False)
     seed: int = SEED
+    force: np.ndarray | None = field(default=None, repr=False)   # [3][nz][ny][nx] added to g
 
     @property
     def ns(self) -> int:
@@ -200,6 +201,31 @@ def random_mixture(lattice: int, shape: tuple, wall_mask: int, M: tuple,
     name = f"random-{'d2q9' if lattice == D2Q9 else 'd3q19'}-{nx}x{ny}x{nz}-ns{ns}"
     return Workload(name, lattice, (nx, ny, nz), wall_mask, tuple(float(m) for m in M), D,
                     tau1, gg, 0, x, nfield, seed)
+
+
+def ultracentrifuge(R: int = 500, H: int = 3, xbar: float = 0.3, C: float = -1.2358e-8,
+                    mass_ratio: float = 0.991481, tau1: float = 0.6, D12: float = 0.08,
+                    steps: int = 2_000_000) -> Workload:
+    """Case II of Sec. 4.2: a binary mixture (the paper's UF6 isotopes, M1/M2 =
+    0.991481) in a cavity of R nodes along the radius r (the y axis, walls at
+    both ends) and H nodes across (periodic), under the centrifugal specific
+    force k(r) = omega^2 r along r, r = the node index.  The constant
+    C = (M1 - M2) omega^2 / (R_U T) of the analytical profile fixes omega^2,
+    with R_U T = M1 c_s1^2 and c_s1^2 = 1/3 (species 1 moves one node per
+    step).  Initial state: mole fractions xbar, 1 - xbar everywhere and total
+    mass density 1 (so n = 1 / sum x_i M_i)."""
+    M1 = 1.0
+    M2 = M1 / mass_ratio
+    omega2 = C * M1 / 3.0 / (M1 - M2)
+    x = np.empty((2, 1, R, H))
+    x[0] = xbar
+    x[1] = 1.0 - xbar
+    n = np.full((1, R, H), 1.0 / (xbar * M1 + (1.0 - xbar) * M2))
+    k = np.zeros((3, 1, R, H))
+    k[1] = (omega2 * np.arange(R, dtype=np.float64))[None, :, None]
+    D = np.array([[0.0, D12], [D12, 0.0]])
+    return Workload(f"ultracentrifuge-d2q9-{H}x{R}", D2Q9, (H, R, 1), WALL_Y, (M1, M2), D, tau1,
+                    (0.0, 0.0, 0.0), steps, x, n, force=k)
 
 
 TUBE_BELOW = {2: (0.9, 0.1), 3: (0.7, 0.2, 0.1)}   # mole fractions in the lower half

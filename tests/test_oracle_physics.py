@@ -134,3 +134,61 @@ def test_shear_wave_decays_with_the_common_viscosity(M, tau1, tol):
     rate = -np.polyfit(times, np.log(amps), 1)[0]
     nu = (tau1 - 0.5) / 3.0
     assert abs(rate / (nu * k * k) - 1) < tol, rate / (nu * k * k)
+
+
+# ---------------------------------------------------------------- force field
+def test_force_field_of_zeros_and_uniform_field_reduce_to_plain_gravity():
+    wl = W.random_mixture(W.D2Q9, (6, 9), W.WALL_Y, (1.0, 2.0, 5.0), g=(1e-5, -2e-5), stream=700)
+    a = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+    a.init(wl.x)
+    a.step(20)
+    b = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+    b.set_force_field(np.zeros((3,) + wl.x.shape[1:]))
+    b.init(wl.x)
+    b.step(20)
+    assert np.array_equal(a.get_f(), b.get_f())
+    # g = 0 plus a uniform field equal to g: F_i = rho_i (0 + g), the same numbers
+    c = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, (0.0, 0.0, 0.0))
+    k = np.zeros((3,) + wl.x.shape[1:])
+    k[0], k[1] = wl.g[0], wl.g[1]
+    c.set_force_field(k)
+    c.init(wl.x)
+    c.step(20)
+    assert np.array_equal(a.get_f(), c.get_f())
+
+
+def _ultracentrifuge_C(x1, r, r_ref):
+    """Least-squares C of ln[x1(r)(1 - x1(r_ref)) / (x1(r_ref)(1 - x1(r)))]
+    = C (r^2 - r_ref^2) / 2, the separation law of Case II."""
+    i0 = list(r).index(r_ref)
+    lhs = np.log(x1 * (1.0 - x1[i0]) / (x1[i0] * (1.0 - x1)))
+    q = (r.astype(float) ** 2 - float(r_ref) ** 2) / 2.0
+    return float((q * lhs).sum() / (q * q).sum())
+
+
+def test_ultracentrifuge_steady_profile_follows_the_closed_form():
+    """Sec. 4.2 Case II: at steady state the separation factor obeys
+    1/alpha = exp(C r^2 / 2) with C = (M1 - M2) omega^2 / (M1 c_s1^2).  A small
+    cavity (R = 48) with a stronger mass contrast (M = 1, 2) and a larger
+    diffusivity reaches steady state quickly (18000 steps, about 15 diffusion
+    times); the fitted C over the bulk rows (away from the wall boundary layer)
+    must match to 1e-4 (observed 3e-6)."""
+    R, H, omega2 = 48, 3, 2e-6
+    wl = W.ultracentrifuge(R=R, H=H, xbar=0.4, tau1=1.0, D12=0.2)
+    wl = W.Workload(wl.name, wl.lattice, wl.shape, wl.wall_mask, (1.0, 2.0), wl.D, wl.tau1, wl.g, 0,
+                    wl.x, np.full(wl.n.shape, 1.0 / (0.4 * 1.0 + 0.6 * 2.0)),
+                    force=np.zeros_like(wl.force))
+    wl.force[1] = (omega2 * np.arange(R))[None, :, None]
+    C = (1.0 - 2.0) * omega2 / (1.0 / 3.0)
+    o = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+    o.set_force_field(wl.force)
+    o.init(wl.x, wl.n)
+    o.step(18000)
+    x1 = o.observables()["x"][0, 0].mean(axis=1)   # average over the periodic width
+    r = np.arange(R)
+    bulk = slice(8, R - 8)
+    Cfit = _ultracentrifuge_C(x1[bulk], r[bulk], 8)
+    assert abs(Cfit / C - 1.0) < 1e-4, (Cfit, C)
+    # and the species mass stays exact up to rounding (T steps x 4 eps)
+    m0 = np.array([(wl.x[i] * wl.M[i] * wl.n).sum() for i in range(2)])
+    assert np.abs(o.mass() / m0 - 1.0).max() < 18000 * 4 * np.finfo(float).eps
