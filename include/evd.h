@@ -198,6 +198,19 @@ long long evd_launch_count(const evd_ctx* ctx);
 evd_status evd_set_kernel(evd_ctx* ctx, int kernel);
 int evd_get_kernel(const evd_ctx* ctx);
 
+/* Per-node specific body force field k(x) added to the uniform g:
+ * F_i(x) = rho_i (g + k(x)) in the moments, the forcing term and the initial
+ * velocities (Eq. first_order_moment_force, Eq. CE_forcing_term_discretized;
+ * the centrifugal force rho_i omega^2 r of Sec. 4.2 Case II is such a field).
+ * k_host: host [D][sites] doubles (component-major, x fastest), finite;
+ * copied to the device in the arithmetic type of the precision.  NULL removes
+ * the field.  Set it before evd_set_fields, whose initial state uses it; it
+ * applies to every later step and readout.  While a field is set the general
+ * kernel runs the step (the TMA-staged step takes a uniform g only):
+ * evd_get_kernel reports EVD_KERNEL_GENERAL and evd_set_kernel(EVD_KERNEL_TMA)
+ * returns EVD_ERR_ARG.  Synchronises. */
+evd_status evd_set_force_field(evd_ctx* ctx, const double* k_host);
+
 /* Rows per tile of the TMA-staged step: 2 (the default; two CTAs of 6 warps
  * per SM for three species) or 4 (one CTA of 12 warps per SM).  Same results;
  * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not

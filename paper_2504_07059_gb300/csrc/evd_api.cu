@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "evd.h"
 #include "evd_internal.h"
@@ -61,6 +62,7 @@ struct evd_ctx {
     int last_parts;      // mass partials written by the last measuring launch
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
+    void* kf;            // per-node force field [3][nsites] in the arithmetic type, or nullptr
     int corr_pending;    // slot of a computed, not yet applied correction, or -1
     int corr_applied;    // slot the last step applied (the readout applies it too), or -1
     long long launches;  // kernels launched by this context
@@ -268,7 +270,7 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
     unsigned* e = c->err_flag;
     cudaStream_t st = c->stream;
     c->launches += 1;
-    if (c->kernel == EVD_KERNEL_TMA) {
+    if (c->kernel == EVD_KERNEL_TMA && !c->kf) {   // the TMA step takes a uniform force only
         const int in = (fin == c->buf[0]) ? 0 : 1;
         c->last_parts = c->tma_blocks;
         if (c->precision == EVD_FP32)
@@ -876,11 +878,42 @@ evd_status evd_set_kernel(evd_ctx* c, int kernel)
         return fail(c, EVD_ERR_ARG, "the TMA-staged step needs D3Q19, FP32 or FP16 storage, walls in x and y "
                                     "and rows of a multiple of 16 bytes");
     if (kernel != EVD_KERNEL_GENERAL && kernel != EVD_KERNEL_TMA) return fail(c, EVD_ERR_ARG, "unknown kernel");
+    if (kernel == EVD_KERNEL_TMA && c->kf)
+        return fail(c, EVD_ERR_ARG, "the TMA-staged step takes a uniform body force only (a force field is set)");
     c->kernel = kernel;
     return EVD_OK;
 }
 
-int evd_get_kernel(const evd_ctx* c) { return c ? c->kernel : 0; }
+int evd_get_kernel(const evd_ctx* c) { return c ? (c->kf ? EVD_KERNEL_GENERAL : c->kernel) : 0; }
+
+evd_status evd_set_force_field(evd_ctx* c, const double* k_host)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (!k_host) {
+        if (c->kf) cudaFree(c->kf);
+        c->kf = nullptr;
+        c->hp.kf = nullptr;
+        return EVD_OK;
+    }
+    const size_t n = (size_t)c->nsites;
+    for (size_t q = 0; q < (size_t)c->D * n; ++q)
+        if (!std::isfinite(k_host[q])) return fail(c, EVD_ERR_ARG, "force field values must be finite");
+    const bool dbl = c->precision == EVD_FP64;
+    const size_t bytes = 3 * n * (dbl ? sizeof(double) : sizeof(float));
+    if (!c->kf) CK(c, cudaMalloc(&c->kf, bytes));
+    // [3][nsites] in the arithmetic type; D2Q9 has no z component
+    std::vector<char> host(bytes, 0);
+    for (int k = 0; k < c->D; ++k)
+        for (size_t q = 0; q < n; ++q) {
+            if (dbl) ((double*)host.data())[k * n + q] = k_host[k * n + q];
+            else ((float*)host.data())[k * n + q] = (float)k_host[k * n + q];
+        }
+    CK(c, cudaMemcpy(c->kf, host.data(), bytes, cudaMemcpyHostToDevice));
+    c->hp.kf = c->kf;
+    return EVD_OK;
+}
 
 evd_status evd_set_tile_rows(evd_ctx* c, int rows)
 {
@@ -934,6 +967,7 @@ evd_status evd_destroy(evd_ctx* c)
     if (c->small) cudaFree(c->small);
     if (c->staging) cudaFree(c->staging);
     if (c->lumps) cudaFree(c->lumps);
+    if (c->kf) cudaFree(c->kf);
     delete c;
     return EVD_OK;
 }

@@ -57,12 +57,14 @@ __device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__
     for (int i = 0; i < NS; ++i) m[i] = 0.0;
     for (int node = node0 + threadIdx.x; node < node0 + count; node += BLOCK) {
         T f[NS][Q];
+        T gn[3];   // specific body force at this node
+        node_force(p, node, gn);
         NodeState<NS, T> s;
         const Nbr nb = neighbours(p, node);
         gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
@@ -116,6 +118,8 @@ __device__ __noinline__ void item_readout(const Params<T>& p, const MemberInfo& 
     for (int i = 0; i < NS; ++i) m[i] = 0.0;
     for (int node = node0 + threadIdx.x; node < node0 + count; node += BLOCK) {
         T f[NS][Q];
+        T gn[3];   // specific body force at this node
+        node_force(p, node, gn);
         NodeState<NS, T> s;
         if (flags & F_RAW) {
             load_raw<LAT, NS>(p, fin, node, f);
@@ -124,7 +128,7 @@ __device__ __noinline__ void item_readout(const Params<T>& p, const MemberInfo& 
             gather_all<LAT, NS>(p, fin, node, nb, f);
             if (corr) add_correction<LAT, NS>(p, corr, f);
         }
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             if (x) x[mi.xoff + i * n + node] = (double)(s.rho[i] * p.Minv[i]) / (double)s.n;
@@ -183,6 +187,8 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
     for (int i = 0; i < NS; ++i) m[i] = 0.0;
     for (int node = node0 + threadIdx.x; node < node0 + count; node += BLOCK) {
         T f[NS][Q];
+        T gn[3];   // specific body force at this node
+        node_force(p, node, gn);
         NodeState<NS, T> s;
         const T nn = nf ? (T)nf[mi.soff + node] : (T)1;
         static_for<0, NS>([&](auto ic) {
@@ -190,7 +196,7 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
             const T r = (T)xf[mi.xoff + I * n + node] * p.M[I] * nn;
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                const T eg = edot<LAT, A>(p.g);
+                const T eg = edot<LAT, A>(gn);
                 f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
             });
         });
@@ -202,9 +208,9 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
                     f[I][A] -= p.ref[I][wclass<LAT>(A)];
                 });
             });
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
         store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
         store_all<LAT, NS>(p, fcur, node, f, s.rho);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];

@@ -143,6 +143,7 @@ struct Params {
     // float storage computes in deviations g = f - ref (see Codec::DARITH):
     T rref[MAXS];          // sum over directions of ref: the density g = 0 stands for
     T refc[MAXS][3];       // wl[class] * rref - ref[class], the rounding of ref, exactly
+    const T* kf;           // per-node specific force [3][nsites] added to g, or nullptr
 };
 
 template <typename T>
@@ -164,6 +165,7 @@ inline Params<T> to_params(const HostParams& h)
             for (int b = 0; b < 3; ++b) p.w2[i][a][b] = (T)h.w2[i][a][b];
         }
     }
+    p.kf = (const T*)h.kf;
     // directions per class: rest, axis, diagonal
     const double n1 = h.lattice == 0 ? 4.0 : 6.0, n2 = h.lattice == 0 ? 4.0 : 12.0;
     for (int i = 0; i < MAXS; ++i) {
@@ -477,6 +479,16 @@ __device__ __forceinline__ T edot(const T (&v)[3])
 }
 
 // -------------------------------------------------- moments and relaxation
+// Specific body force at a node: the uniform g plus the node's entry of the
+// force field when one is set (F_i = rho_i (g + k(x)); Case II of Sec. 4.2
+// is such a field).
+template <typename T>
+__device__ __forceinline__ void node_force(const Params<T>& p, int node, T (&g)[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = p.kf ? p.g[k] + p.kf[(long long)k * p.nsites + node] : p.g[k];
+}
+
 template <int NS, typename T>
 struct NodeState {
     T rho[NS];
@@ -496,7 +508,7 @@ struct NodeState {
 // j_i = sum e g (the references cancel in j).
 template <int LAT, int NS, bool DA = false, typename T>
 __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat<LAT>::Q],
-                                        NodeState<NS, T>& s, unsigned& err)
+                                        NodeState<NS, T>& s, unsigned& err, const T (&g)[3])
 {
     constexpr int Q = Lat<LAT>::Q;
     s.rho_mix = (T)0;
@@ -521,7 +533,7 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
         const T rinv = (T)1 / r;
         s.rho[I] = r;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) s.ueq[I][k] = p.c[I] * j[k] * rinv + (T)0.5 * p.g[k];
+        for (int k = 0; k < 3; ++k) s.ueq[I][k] = p.c[I] * j[k] * rinv + (T)0.5 * g[k];
         s.rho_mix += r;
         s.n += r * p.Minv[I];
     });
@@ -590,11 +602,11 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 //      B = 1/tau + b, b = (e-u).a / c_s^2 (the same algebra as above, minus ref).
 template <int LAT, int NS, bool DA = false, typename T>
 __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
-                                        const NodeState<NS, T>& s)
+                                        const NodeState<NS, T>& s, const T (&g)[3])
 {
     constexpr int Q = Lat<LAT>::Q;
     const T usq = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
-    const T ug = s.u[0] * p.g[0] + s.u[1] * p.g[1] + s.u[2] * p.g[2];
+    const T ug = s.u[0] * g[0] + s.u[1] * g[1] + s.u[2] * g[2];
     T av[NS][3], Bc[NS], U2[NS], wr[NS][3], sr[NS], Bm[NS], dt[NS][3];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -618,7 +630,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
         constexpr int A = decltype(ac)::value;
         constexpr int C = wclass<LAT>(A);
         const T eu = edot<LAT, A>(s.u);
-        const T eg = edot<LAT, A>(p.g);
+        const T eg = edot<LAT, A>(g);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const T ea = edot<LAT, A>(av[i]);
@@ -690,14 +702,16 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
     const int node = blockIdx.x * BLOCK + threadIdx.x;
     const bool active = node < p.nsites;
     T f[NS][Q];
+    T gn[3] = {p.g[0], p.g[1], p.g[2]};   // specific body force at this node
+    if (active) node_force(p, node, gn);
     NodeState<NS, T> s;
     unsigned err = 0;
     if (active) {
         const Nbr nb = neighbours(p, node);
         gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }
@@ -717,6 +731,8 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
     const int node = blockIdx.x * BLOCK + threadIdx.x;
     const bool active = node < p.nsites;
     T f[NS][Q];
+    T gn[3] = {p.g[0], p.g[1], p.g[2]};   // specific body force at this node
+    if (active) node_force(p, node, gn);
     NodeState<NS, T> s;
     unsigned err = 0;
     if (active) {
@@ -727,7 +743,7 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
             gather_all<LAT, NS>(p, fin, node, nb, f);
             if (corr) add_correction<LAT, NS>(p, corr, f);   // as the last step saw f_t
         }
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
         const long long ns_ = p.nsites;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -769,6 +785,8 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
     const int node = blockIdx.x * BLOCK + threadIdx.x;
     const bool active = node < p.nsites;
     T f[NS][Q];
+    T gn[3] = {p.g[0], p.g[1], p.g[2]};   // specific body force at this node
+    if (active) node_force(p, node, gn);
     NodeState<NS, T> s;
     unsigned err = 0;
     if (active) {
@@ -785,7 +803,7 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
                 const T r = (T)xf[I * ns_ + node] * p.M[I] * n;
                 static_for<0, Q>([&](auto ac) {
                     constexpr int A = decltype(ac)::value;
-                    const T eg = edot<LAT, A>(p.g);
+                    const T eg = edot<LAT, A>(gn);
                     f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
                 });
             });
@@ -798,9 +816,9 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
                     f[I][A] -= p.ref[I][wclass<LAT>(A)];
                 });
             });
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
         store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s);
+        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
         store_all<LAT, NS>(p, fcur, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }

@@ -32,6 +32,7 @@ struct HostParams {
     double w1[MAXS][3], w2[MAXS][3][3];
     double wl[3];
     double ref[MAXS][3];
+    const void* kf;          // device [3][nsites] force field in the arithmetic type, or nullptr
 };
 
 // Host-side checks and constants shared by the single-lattice context and the

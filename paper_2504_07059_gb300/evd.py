@@ -83,6 +83,7 @@ _SIGNATURES = {
     "evd_set_kernel": (_st, [_vp, ctypes.c_int]),
     "evd_get_kernel": (ctypes.c_int, [_vp]),
     "evd_set_tile_rows": (_st, [_vp, ctypes.c_int]),
+    "evd_set_force_field": (_st, [_vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
@@ -288,6 +289,11 @@ def evd_get_kernel(ctx) -> int:
     return lib().evd_get_kernel(ctx)
 
 
+def evd_set_force_field(ctx, k=None):
+    """k: [D][sites] float64 (host), or None to remove the field."""
+    _check(lib().evd_set_force_field(ctx, _ptr(k)), ctx)
+
+
 def evd_set_tile_rows(ctx, rows: int):
     _check(lib().evd_set_tile_rows(ctx, int(rows)), ctx)
 
@@ -424,6 +430,8 @@ class Simulation:
     @classmethod
     def from_workload(cls, wl, precision="fp64", stream=None):
         sim = cls(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, precision, stream)
+        if getattr(wl, "force", None) is not None:
+            sim.set_force_field(wl.force)
         sim.set_fields(wl.x, wl.n)
         return sim
 
@@ -442,6 +450,14 @@ class Simulation:
         x = np.ascontiguousarray(x, dtype=np.float64)
         n = None if n is None else np.ascontiguousarray(n, dtype=np.float64)
         evd_set_fields(self.ctx, x, n)
+
+    def set_force_field(self, k):
+        """Per-node specific force (3 or D, nz, ny, nx) added to g; None removes it."""
+        if k is None:
+            evd_set_force_field(self.ctx, None)
+            return
+        k = np.ascontiguousarray(np.asarray(k, dtype=np.float64)[:self.D]).reshape(self.D, -1)
+        evd_set_force_field(self.ctx, np.ascontiguousarray(k))
 
     def set_populations(self, f):
         evd_set_populations(self.ctx, np.ascontiguousarray(f, dtype=np.float64))

@@ -1,0 +1,99 @@
+"""The per-node body-force field (evd_set_force_field) on the GPU: parity with
+the oracle carrying the same field, kernel selection, and the ultracentrifuge
+of Sec. 4.2 (Case II) at the paper's size against its closed form."""
+import numpy as np
+import pytest
+
+from paper_2504_07059_gb300 import workloads as W
+from parity_utils import TOL_MASS, TOL_X, compare_all_fp64, gpu_run, max_rel, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def with_field(wl, amp, stream):
+    """The workload with a seeded random field of amplitude amp added to g."""
+    u = W.uniform01(stream, 3 * wl.nsites, wl.seed).reshape((3,) + wl.x.shape[1:])
+    k = amp * (2.0 * u - 1.0)
+    if wl.lattice == W.D2Q9:
+        k[2] = 0.0
+    wl.force = k
+    return wl
+
+
+CASES = {
+    "d2q9-ternary-walls": (lambda: with_field(W.random_mixture(W.D2Q9, (17, 23), W.WALL_X | W.WALL_Y,
+                                                               (1.0, 3.0, 7.0), g=(1e-5, -2e-5), stream=900),
+                                              2e-4, 901), 40),
+    "d2q9-binary-periodic": (lambda: with_field(W.random_mixture(W.D2Q9, (12, 9), 0, (1.0, 2.5), stream=910),
+                                                1e-4, 911), 40),
+    "d3q19-ternary-box": (lambda: with_field(W.random_mixture(W.D3Q19, (9, 8, 7), W.WALL_X | W.WALL_Y | W.WALL_Z,
+                                                              (16.0, 28.0, 44.0), g=(0, -2e-6, 0), stream=920),
+                                             1e-4, 921), 15),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_force_field_matches_the_oracle_on_every_field(evd, name):
+    make, steps = CASES[name]
+    wl = make()
+    o = oracle_run(wl, steps)
+    sim = gpu_run(evd, wl, steps, "fp64")
+    compare_all_fp64(sim, o)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("name", ["d2q9-ternary-walls", "d3q19-ternary-box"])
+def test_reduced_precision_force_field(evd, name, precision):
+    make, steps = CASES[name]
+    wl = make()
+    o = oracle_run(wl, steps)
+    sim = gpu_run(evd, wl, steps, precision)
+    assert np.abs(sim.mole_fractions() - o.observables()["x"]).max() < TOL_X[precision]
+    m0 = np.array([(wl.x[i] * wl.M[i]).sum() for i in range(wl.ns)])
+    assert max_rel(sim.species_mass(), m0) < TOL_MASS[precision]
+    sim.close()
+
+
+def test_a_field_selects_the_general_kernel(evd):
+    make, _ = CASES["d3q19-ternary-box"]
+    wl = make()
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp32")
+    assert evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_TMA
+    sim.set_force_field(wl.force)
+    assert evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_GENERAL
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_set_kernel(sim.ctx, evd.EVD_KERNEL_TMA)
+    assert ei.value.status == evd.EVD_ERR_ARG
+    sim.set_force_field(None)
+    assert evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_TMA
+    sim.close()
+
+
+def _fit_C(x1, r, r_ref):
+    i0 = list(r).index(r_ref)
+    lhs = np.log(x1 * (1.0 - x1[i0]) / (x1[i0] * (1.0 - x1)))
+    q = (r.astype(float) ** 2 - float(r_ref) ** 2) / 2.0
+    return float((q * lhs).sum() / (q * q).sum())
+
+
+def test_ultracentrifuge_case_ii_at_the_papers_size(evd):
+    """Case II as the paper sets it up (R = 500, H = 3, UF6 isotopes,
+    C = -1.2358e-8, tau1 = 0.6, D12 = 0.08, xbar = 0.3 and 0.7), FP64, run
+    about seven diffusion times R^2/(pi^2 D) to steady state: the separation
+    law 1/alpha = exp(C r^2/2) fitted over the bulk rows gives C within 1e-3,
+    and the two mean compositions give the same separation factor."""
+    fits, alphas = [], []
+    for xbar in (0.3, 0.7):
+        wl = W.ultracentrifuge(xbar=xbar)
+        sim = gpu_run(evd, wl, 2_200_000, "fp64")
+        x1 = sim.mole_fractions()[0, 0].mean(axis=1)
+        sim.check()
+        sim.close()
+        r = np.arange(500)
+        bulk = slice(8, 492)
+        fits.append(_fit_C(x1[bulk], r[bulk], 8))
+        alphas.append(x1[8] * (1.0 - x1) / ((1.0 - x1[8]) * x1))
+    for c in fits:
+        assert abs(c / -1.2358e-8 - 1.0) < 1e-3, fits
+    assert np.abs(alphas[0][8:492] - alphas[1][8:492]).max() < 1e-6
