@@ -38,7 +38,13 @@ typedef struct {
     double tau1;          /* self relaxation time of the lightest species         */
     double g[3];          /* specific body force: F_i = rho_i g                   */
     int tau_mode;         /* 0: closed forms for ns<=3, 1: dense solve always     */
+    unsigned flags;       /* corrective forcing terms of Eq. (improved_forcing_scheme):
+                             bit 0 S_diff, bit 1 S_p, bit 2 S_rho; 0 = standard term */
 } or_config;
+
+#define OR_S_DIFF 1u
+#define OR_S_P 2u
+#define OR_S_RHO 4u
 
 typedef struct {
     double rho[OR_MAXS];
@@ -65,6 +71,7 @@ typedef struct {
     double c[OR_MAXS], cs2[OR_MAXS], tau[OR_MAXS];
     double *f, *fs, *fn;  /* [ns][Q][nsites] */
     double* acc;          /* [3][nsites] per-node specific force added to g, or NULL */
+    double* rho_field;    /* [ns][nsites] densities of f_t, for the gradient terms */
     long t;
 } or_state;
 
@@ -274,7 +281,10 @@ static void node_force(const or_state* st, long X, double a[3])
  *                                     + (1 - dt/(2 tau_i)) S^i
  * f and fstar are [ns][Q] for this node.  Returns 0 on a non-positive density.
  */
-static int collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg, const double* acc)
+/* grad: NULL, or per node the gradients of the species densities [ns][3]
+ * followed by the gradient of the mixture density [3], for S_p and S_rho. */
+static int collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg, const double* acc,
+                        const double* grad)
 {
     const or_config* cfg = &st->cfg;
     const int ns = cfg->ns, Q = st->Q;
@@ -304,6 +314,22 @@ static int collide_node(const or_state* st, const double* f, double* fstar, or_d
 
     for (i = 0; i < ns; ++i) {
         const double cs2 = st->cs2[i], tau_i = st->tau[i];
+        /* corrective terms (Eq. improved_forcing_scheme): the vectors they
+         * contract with [(e e - cs2 I)/cs2^2 . u] (S_diff: Theta_i dt/(2 tau_i
+         * - dt); S_p, with a minus sign: grad(rho_i cs2)) and with
+         * [(e e - cs2 I)/cs2 . u_i^eq] (S_rho: w_i grad rho, w_i = rho_i/rho) */
+        double Xc[3] = {0, 0, 0}, Yc[3] = {0, 0, 0};
+        if (cfg->flags & OR_S_DIFF)
+            for (k = 0; k < 3; ++k) {
+                double th = 0.0;
+                for (j = 0; j < ns; ++j)
+                    if (j != i) th += rho[i] * rho[j] / (rho_mix * tau_x[i * ns + j]) * (ueq[i][k] - ueq[j][k]);
+                Xc[k] += dt / (2.0 * tau_i - dt) * th;
+            }
+        if ((cfg->flags & OR_S_P) && grad)
+            for (k = 0; k < 3; ++k) Xc[k] -= cs2 * grad[i * 3 + k];
+        if ((cfg->flags & OR_S_RHO) && grad)
+            for (k = 0; k < 3; ++k) Yc[k] = (rho[i] / rho_mix) * grad[ns * 3 + k];
         for (a = 0; a < Q; ++a) {
             double ei[3], emu[3], eu = 0.0, usq = 0.0, proj = 0.0, feq, f0, om_self, om_cross = 0.0, S = 0.0;
             for (k = 0; k < 3; ++k) {
@@ -329,6 +355,15 @@ static int collide_node(const or_state* st, const double* f, double* fstar, or_d
                 for (l = 0; l < 3; ++l)
                     v += (ei[k] * ei[l] - cs2 * (k == l ? 1.0 : 0.0)) / (cs2 * cs2) * u[l];
                 S += v * F[i][k];
+            }
+            if (cfg->flags) {
+                double corr = 0.0;
+                for (k = 0; k < 3; ++k)
+                    for (l = 0; l < 3; ++l) {
+                        const double t = ei[k] * ei[l] - cs2 * (k == l ? 1.0 : 0.0);
+                        corr += t / (cs2 * cs2) * u[l] * Xc[k] + t / cs2 * ueq[i][l] * Yc[k];
+                    }
+                S += corr;
             }
             S *= st->w[a];
             fstar[i * Q + a] = f[i * Q + a] + om_self + om_cross + (1.0 - dt / (2.0 * tau_i)) * S;
@@ -465,7 +500,7 @@ or_state* or_create(const or_config* cfg)
 void or_destroy(or_state* st)
 {
     if (!st) return;
-    free(st->f); free(st->fs); free(st->fn); free(st->acc); free(st);
+    free(st->f); free(st->fs); free(st->fn); free(st->acc); free(st->rho_field); free(st);
 }
 
 /* Per-node specific force field k(x), [3][nsites] (x fastest inside each
@@ -536,20 +571,71 @@ void or_get_f(const or_state* st, double* f)
 long or_time(const or_state* st) { return st->t; }
 
 /* One collision of every node into st->fs.  Returns 0 on failure. */
+/* Isotropic lattice gradient of a node field phi at X (a reading: the paper
+ * does not say how the gradients of Eq. improved_forcing_scheme are
+ * discretised): grad phi = (1/cs0^2) sum_a w_a e_a phi(X + e_a) with the unit
+ * lattice's weights and cs0^2 = 1/3.  A neighbour beyond an impermeable wall
+ * takes the value at X (zero normal gradient); periodic faces wrap. */
+static void lattice_grad(const or_state* st, const double* phi, long X, double g[3])
+{
+    const or_config* cfg = &st->cfg;
+    const int ext[3] = {cfg->nx, cfg->ny, cfg->nz};
+    const long stride[3] = {1, cfg->nx, (long)cfg->nx * cfg->ny};
+    const int crd[3] = {(int)(X % cfg->nx), (int)((X / cfg->nx) % cfg->ny), (int)(X / stride[2])};
+    int a, k;
+    g[0] = g[1] = g[2] = 0.0;
+    for (a = 0; a < st->Q; ++a) {
+        long Y = 0;
+        int solid = 0;
+        for (k = 0; k < 3; ++k) {
+            int c = crd[k] + st->e[a][k];
+            if (c < 0 || c >= ext[k]) {
+                if ((cfg->wall_mask >> (2 * k)) & 3u) solid = 1;
+                c = (c + ext[k]) % ext[k];
+            }
+            Y += c * stride[k];
+        }
+        {
+            const double v = solid ? phi[X] : phi[Y];
+            for (k = 0; k < 3; ++k) g[k] += st->w[a] * st->e[a][k] * v;
+        }
+    }
+    for (k = 0; k < 3; ++k) g[k] *= 3.0;
+}
+
 static int collide_all(or_state* st)
 {
     const int ns = st->cfg.ns, Q = st->Q;
     const long nsites = st->nsites;
     double fn[OR_MAXS * OR_MAXQ] = {0}, fo[OR_MAXS * OR_MAXQ] = {0};
+    double grad[(OR_MAXS + 1) * 3];
+    const int need_grad = (st->cfg.flags & (OR_S_P | OR_S_RHO)) != 0;
     int i, a;
     long X;
+    if (need_grad) {
+        /* densities of f_t at every node first: rho_i, then the mixture */
+        if (!st->rho_field) st->rho_field = (double*)malloc(sizeof(double) * (size_t)(ns + 1) * nsites);
+        if (!st->rho_field) return 0;
+        for (X = 0; X < nsites; ++X) {
+            double r = 0.0;
+            for (i = 0; i < ns; ++i) {
+                double ri = 0.0;
+                for (a = 0; a < Q; ++a) ri += st->f[((long)i * Q + a) * nsites + X];
+                st->rho_field[(long)i * nsites + X] = ri;
+                r += ri;
+            }
+            st->rho_field[(long)ns * nsites + X] = r;
+        }
+    }
     for (X = 0; X < nsites; ++X) {
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) fn[i * Q + a] = st->f[((long)i * Q + a) * nsites + X];
+        if (need_grad)
+            for (i = 0; i <= ns; ++i) lattice_grad(st, st->rho_field + (long)i * nsites, X, grad + i * 3);
         {
             double acc[3];
             node_force(st, X, acc);
-            if (!collide_node(st, fn, fo, NULL, acc)) return 0;
+            if (!collide_node(st, fn, fo, NULL, acc, need_grad ? grad : NULL)) return 0;
         }
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) st->fs[((long)i * Q + a) * nsites + X] = fo[i * Q + a];
@@ -592,7 +678,7 @@ int or_collide_only(or_state* st)
 /* One node through the collision, with every intermediate term returned. */
 int or_collide_node(const or_state* st, const double* f, double* fstar, or_diag* dg)
 {
-    return collide_node(st, f, fstar, dg, st->cfg.g);
+    return collide_node(st, f, fstar, dg, st->cfg.g, NULL);
 }
 
 int or_diag_size(void) { return (int)sizeof(or_diag); }
@@ -617,7 +703,7 @@ int or_observables(const or_state* st, double* x, double* rho, double* u, double
         {
             double acc[3];
             node_force(st, X, acc);
-            if (!collide_node(st, fn, fo, &dg, acc)) return 0;
+            if (!collide_node(st, fn, fo, &dg, acc, NULL)) return 0;
         }
         for (i = 0; i < ns; ++i) {
             if (x) x[(long)i * nsites + X] = dg.rho[i] / (dg.n * st->cfg.M[i]);

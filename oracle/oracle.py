@@ -56,7 +56,12 @@ class Config(ctypes.Structure):
         ("tau1", ctypes.c_double),
         ("g", ctypes.c_double * 3),
         ("tau_mode", ctypes.c_int),
+        ("flags", ctypes.c_uint),
     ]
+
+
+# corrective forcing terms of Eq. (improved_forcing_scheme), Config.flags bits
+S_DIFF, S_P, S_RHO = 1, 2, 4
 
 
 class Diag(ctypes.Structure):
@@ -134,7 +139,7 @@ def lattice_info(lattice: int):
             np.array(opp[:Q], dtype=np.int64))
 
 
-def make_config(lattice, shape, wall_mask, M, D, tau1, g, tau_mode=0) -> Config:
+def make_config(lattice, shape, wall_mask, M, D, tau1, g, tau_mode=0, flags=0) -> Config:
     nx, ny, nz = (tuple(shape) + (1, 1))[:3]
     ns = len(M)
     c = Config()
@@ -153,6 +158,7 @@ def make_config(lattice, shape, wall_mask, M, D, tau1, g, tau_mode=0) -> Config:
     for k in range(3):
         c.g[k] = float(gg[k])
     c.tau_mode = int(tau_mode)
+    c.flags = int(flags)
     return c
 
 
@@ -169,8 +175,8 @@ def tau_cross(cfg: Config, rho, dense: bool = False) -> np.ndarray:
 class Oracle:
     """One lattice in the oracle.  ``shape`` is (nx, ny[, nz])."""
 
-    def __init__(self, lattice, shape, wall_mask, M, D, tau1, g, tau_mode=0):
-        self.cfg = make_config(lattice, shape, wall_mask, M, D, tau1, g, tau_mode)
+    def __init__(self, lattice, shape, wall_mask, M, D, tau1, g, tau_mode=0, flags=0):
+        self.cfg = make_config(lattice, shape, wall_mask, M, D, tau1, g, tau_mode, flags)
         self.lattice = int(lattice)
         self.ns = len(M)
         self.Q = 9 if lattice == 0 else 19

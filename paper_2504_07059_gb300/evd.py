@@ -415,10 +415,10 @@ class Simulation:
     site axes in (nz, ny, nx) order, matching the seeded workloads."""
 
     def __init__(self, lattice, shape, wall_mask, molar_mass, diffusivity, tau1, g=(0.0, 0.0, 0.0),
-                 precision="fp64", stream=None):
+                 precision="fp64", stream=None, flags=0):
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.grid = make_grid(lattice, self.precision, shape, wall_mask)
-        self.species = SpeciesTable(molar_mass, diffusivity, tau1, g)
+        self.species = SpeciesTable(molar_mass, diffusivity, tau1, g, flags)
         self.lattice = int(lattice)
         self.ns = len(self.species.M)
         self.Q = 9 if self.lattice == EVD_D2Q9 else 19
@@ -429,7 +429,8 @@ class Simulation:
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", stream=None):
-        sim = cls(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, precision, stream)
+        sim = cls(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, precision, stream,
+                  getattr(wl, "flags", 0))
         if getattr(wl, "force", None) is not None:
             sim.set_force_field(wl.force)
         sim.set_fields(wl.x, wl.n)

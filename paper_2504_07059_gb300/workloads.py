@@ -74,6 +74,7 @@ class Workload:
     n: np.ndarray | None = field(default=None, repr=False)
     seed: int = SEED
     force: np.ndarray | None = field(default=None, repr=False)   # [3][nz][ny][nx] added to g
+    flags: int = 0          # corrective forcing terms (bit 0 S_diff, 1 S_p, 2 S_rho)
 
     @property
     def ns(self) -> int:

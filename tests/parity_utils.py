@@ -15,7 +15,8 @@ TOL_MASS = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-6}
 
 
 def oracle_run(wl: W.Workload, steps: int) -> O.Oracle:
-    o = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g)
+    o = O.Oracle(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g,
+                 flags=getattr(wl, "flags", 0))
     if getattr(wl, "force", None) is not None:
         o.set_force_field(wl.force)
     o.init(wl.x, wl.n)
