@@ -94,6 +94,20 @@ typedef struct {
     unsigned wall_mask;   /* EVD_WALL_* bits                                       */
 } evd_grid;
 
+/* Corrective forcing terms of Eq. (improved_forcing_scheme), added to the
+ * standard forcing term (Sec. 3; the paper finds them negligible in its cases,
+ * Sec. 4.3):
+ *   EVD_FORCE_S_DIFF  w [(e e - cs2 I)/cs2^2 . u] . Theta_i dt/(2 tau_i - dt)
+ *   EVD_FORCE_S_P     - w [(e e - cs2 I)/cs2^2 . u] . grad(rho_i cs2)
+ *   EVD_FORCE_S_RHO   w [(e e - cs2 I)/cs2 . u_i^eq] . (w_i grad rho)
+ * Gradients: the isotropic lattice gradient (1/cs0^2) sum_a w_a e_a phi(x+e_a)
+ * of the densities of f_t (the paper does not give one), a neighbour beyond a
+ * wall taking the node's value.  D2Q9 only (EVD_ERR_ARG for D3Q19); the
+ * gradient terms add one density pass over the populations per step. */
+#define EVD_FORCE_S_DIFF 1u
+#define EVD_FORCE_S_P 2u
+#define EVD_FORCE_S_RHO 4u
+
 typedef struct {
     int n_species;             /* 1 .. EVD_MAX_SPECIES                              */
     const double* molar_mass;  /* [n_species], > 0, non-decreasing                  */
@@ -102,7 +116,7 @@ typedef struct {
     double tau1;               /* self relaxation time of species 0, > 1/2; the     */
                                /* others follow from equal kinematic viscosity       */
     double g[3];               /* specific body force, F_i = rho_i g (gravity)       */
-    unsigned flags;            /* reserved, must be 0                                */
+    unsigned flags;            /* EVD_FORCE_* corrective forcing terms, or 0          */
 } evd_species;
 
 typedef struct evd_ctx evd_ctx;

@@ -63,6 +63,7 @@ struct evd_ctx {
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
     void* kf;            // per-node force field [3][nsites] in the arithmetic type, or nullptr
+    void* rhof;          // [ns + 1][nsites] densities of f_t for the gradient terms, or nullptr
     int corr_pending;    // slot of a computed, not yet applied correction, or -1
     int corr_applied;    // slot the last step applied (the readout applies it too), or -1
     long long launches;  // kernels launched by this context
@@ -149,7 +150,11 @@ bool validate(const evd_grid* g, const evd_species* s, std::string& msg)
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(s->g[k])) { msg = "g must be finite"; return false; }
     if (g->lattice == EVD_D2Q9 && s->g[2] != 0.0) { msg = "D2Q9 needs g[2] == 0"; return false; }
-    if (s->flags != 0) { msg = "flags must be 0"; return false; }
+    if (s->flags & ~(EVD_FORCE_S_DIFF | EVD_FORCE_S_P | EVD_FORCE_S_RHO)) { msg = "unknown species flags"; return false; }
+    if (s->flags && g->lattice != EVD_D2Q9) {
+        msg = "the corrective forcing terms are implemented for D2Q9";
+        return false;
+    }
     return true;
 }
 
@@ -190,6 +195,7 @@ void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
     h.nx = g->nx; h.ny = g->ny; h.nz = g->nz;
     h.nsites = g->nx * g->ny * g->nz;
     h.pstride = plane_stride(g);
+    h.flags = s->flags;
     for (int k = 0; k < 3; ++k) {
         h.wall[k] = ((g->wall_mask >> (2 * k)) & 3u) ? 1 : 0;
         h.g[k] = s->g[k];
@@ -278,6 +284,18 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
         return evd::launch_step_tma<2>(h, c->tma_ty, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
     }
     c->last_parts = c->nblocks;
+    if (h.flags) {   // corrective forcing terms (D2Q9): densities of f_t first when gradients are needed
+        if (h.rhof) {
+            c->launches += 1;
+            const cudaError_t ed = c->precision == EVD_FP64 ? evd::CorrLaunch<0>::density(h, fin, corr, st)
+                                 : c->precision == EVD_FP32 ? evd::CorrLaunch<1>::density(h, fin, corr, st)
+                                                            : evd::CorrLaunch<2>::density(h, fin, corr, st);
+            if (ed != cudaSuccess) return ed;
+        }
+        if (c->precision == EVD_FP64) return evd::CorrLaunch<0>::step(h, fin, fout, mp, e, flags, corr, st);
+        if (c->precision == EVD_FP32) return evd::CorrLaunch<1>::step(h, fin, fout, mp, e, flags, corr, st);
+        return evd::CorrLaunch<2>::step(h, fin, fout, mp, e, flags, corr, st);
+    }
     switch (c->precision * 2 + c->lattice) {
         case 0: return evd::Launch<0, 0>::step(h, fin, fout, mp, e, flags, corr, st);
         case 1: return evd::Launch<0, 1>::step(h, fin, fout, mp, e, flags, corr, st);
@@ -581,6 +599,17 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
                 return cuda_fail(nullptr, e, "cudaMalloc(populations)");
             }
         }
+    }
+    if (c->hp.flags & (EVD_FORCE_S_P | EVD_FORCE_S_RHO)) {
+        // densities of f_t at every node, for the gradient terms
+        const size_t rb = (size_t)(c->ns + 1) * c->nsites * (c->precision == EVD_FP64 ? sizeof(double) : sizeof(float));
+        e = cudaMalloc(&c->rhof, rb);
+        if (e != cudaSuccess) {
+            if (c->own_bufs) { cudaFree(c->buf[0]); cudaFree(c->buf[1]); }
+            delete c;
+            return cuda_fail(nullptr, e, "cudaMalloc(density field)");
+        }
+        c->hp.rhof = c->rhof;
     }
     c->tma_ty = kTmaRows;
     c->tma_ok = tma_setup(c);
@@ -968,6 +997,7 @@ evd_status evd_destroy(evd_ctx* c)
     if (c->staging) cudaFree(c->staging);
     if (c->lumps) cudaFree(c->lumps);
     if (c->kf) cudaFree(c->kf);
+    if (c->rhof) cudaFree(c->rhof);
     delete c;
     return EVD_OK;
 }

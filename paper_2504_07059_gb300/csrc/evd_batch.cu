@@ -424,7 +424,8 @@ evd_status evd_batch_create(int lattice, int precision, const evd_member* member
         const evd_member& mb = members[m];
         const evd_grid g{lattice, precision, mb.nx, mb.ny, mb.nz, mb.wall_mask};
         std::string msg;
-        if (!evd::validate(&g, &mb.species, msg)) {
+        if (mb.species.flags) msg = "the corrective forcing terms are not supported in a batch";
+        if (!msg.empty() || !evd::validate(&g, &mb.species, msg)) {
             delete b;
             return fail(nullptr, EVD_ERR_ARG, "member " + std::to_string(m) + ": " + msg);
         }

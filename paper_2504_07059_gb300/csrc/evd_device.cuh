@@ -144,6 +144,8 @@ struct Params {
     T rref[MAXS];          // sum over directions of ref: the density g = 0 stands for
     T refc[MAXS][3];       // wl[class] * rref - ref[class], the rounding of ref, exactly
     const T* kf;           // per-node specific force [3][nsites] added to g, or nullptr
+    unsigned flags;        // corrective forcing terms: bit 0 S_diff, 1 S_p, 2 S_rho
+    const T* rhof;         // [ns + 1][nsites] densities of f_t (species, mixture) or nullptr
 };
 
 template <typename T>
@@ -166,6 +168,8 @@ inline Params<T> to_params(const HostParams& h)
         }
     }
     p.kf = (const T*)h.kf;
+    p.flags = h.flags;
+    p.rhof = (const T*)h.rhof;
     // directions per class: rest, axis, diagonal
     const double n1 = h.lattice == 0 ? 4.0 : 6.0, n2 = h.lattice == 0 ? 4.0 : 12.0;
     for (int i = 0; i < MAXS; ++i) {
@@ -600,11 +604,33 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 // (1 - 1/tau = omt exactly on the float grid of the constants)
 // with feq = w rho (1 + phi), phi = t1 (1 + t1/2) - u^2/(2 c_s^2),
 //      B = 1/tau + b, b = (e-u).a / c_s^2 (the same algebra as above, minus ref).
-template <int LAT, int NS, bool DA = false, typename T>
+// CORR: add the corrective terms of Eq. (improved_forcing_scheme) that
+// p.flags selects (they are part of S, so the update scales them by
+// 1 - 1/(2 tau_i)): with e = c_i e_hat,
+//   S_diff = w [(e e - cs2 I)/cs2^2 . u] . Theta_i dt/(2 tau_i - dt),
+//   S_p    = w [(e e - cs2 I)/cs2^2 . u] . grad(rho_i cs2)      (subtracted),
+//   S_rho  = w [(e e - cs2 I)/cs2 . u_i^eq] . (w_i grad rho),   w_i = rho_i/rho;
+// grad: [NS + 1][3] lattice gradients of rho_i and rho at this node.
+template <int LAT, int NS, bool DA = false, bool CORR = false, typename T>
 __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
-                                        const NodeState<NS, T>& s, const T (&g)[3])
+                                        const NodeState<NS, T>& s, const T (&g)[3],
+                                        const T (*grad)[3] = nullptr)
 {
     constexpr int Q = Lat<LAT>::Q;
+    T Xc[NS][3], Yc[NS][3];   // the vectors the corrective terms contract with
+    if constexpr (CORR) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const T tau_i = (T)1 / p.tau_inv[i];
+            const T cs2 = (T)1 / p.inv_cs2[i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Xc[i][k] = (p.flags & 1u) ? s.rho[i] * s.V[i][k] / ((T)2 * tau_i - (T)1) : (T)0;   // Theta_i = rho_i V_i
+                if (p.flags & 2u) Xc[i][k] -= cs2 * grad[i][k];
+                Yc[i][k] = (p.flags & 4u) ? s.rho[i] / s.rho_mix * grad[NS][k] : (T)0;
+            }
+        }
+    }
     const T usq = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
     const T ug = s.u[0] * g[0] + s.u[1] * g[1] + s.u[2] * g[2];
     T av[NS][3], Bc[NS], U2[NS], wr[NS][3], sr[NS], Bm[NS], dt[NS][3];
@@ -635,7 +661,17 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
         for (int i = 0; i < NS; ++i) {
             const T ea = edot<LAT, A>(av[i]);
             const T t1 = p.c_inv_cs2[i] * eu;                       // e.u / c_s^2
-            const T S = p.wl[C] * sr[i] * fma(p.c[i] * eg, (T)1 + t1, -ug);
+            T S = p.wl[C] * sr[i] * fma(p.c[i] * eg, (T)1 + t1, -ug);
+            if constexpr (CORR) {
+                const T eX = edot<LAT, A>(Xc[i]), eY = edot<LAT, A>(Yc[i]);
+                const T uX = s.u[0] * Xc[i][0] + s.u[1] * Xc[i][1] + s.u[2] * Xc[i][2];
+                const T qY = s.ueq[i][0] * Yc[i][0] + s.ueq[i][1] * Yc[i][1] + s.ueq[i][2] * Yc[i][2];
+                const T eq = edot<LAT, A>(s.ueq[i]);
+                const T c2 = p.c[i] * p.c[i];
+                // ((e.u)(e.X) - cs2 u.X)/cs2^2 + ((e.u^eq)(e.Y) - cs2 u^eq.Y)/cs2, e = c e_hat
+                const T corr = p.inv_cs2[i] * (p.inv_cs2[i] * c2 * eu * eX - uX) + (p.inv_cs2[i] * c2 * eq * eY - qY);
+                S += p.wl[C] * p.sfac[i] * corr;
+            }
             if constexpr (DA) {
                 const T phi = fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T b = fma(p.c_inv_cs2[i], ea, Bm[i]);
@@ -712,6 +748,87 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
         if (corr) add_correction<LAT, NS>(p, corr, f);
         moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
         collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
+        store_all<LAT, NS>(p, fout, node, f, s.rho);
+        if (err) atomicOr(err_flag, err);
+    }
+    if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
+}
+
+// Densities of f_t at every node (the gather and correction of k_step, then
+// rho_i and rho), for the gradients of the corrective terms: rhof [NS + 1][nsites].
+template <int LAT, int NS, typename S, typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_density(const Params<T> p, const S* __restrict__ fin, T* __restrict__ rhof, const double* __restrict__ corr)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    if (node >= p.nsites) return;
+    T f[NS][Q];
+    const Nbr nb = neighbours(p, node);
+    gather_all<LAT, NS>(p, fin, node, nb, f);
+    if (corr) add_correction<LAT, NS>(p, corr, f);
+    T mix = (T)0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        T r = (T)0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) r += f[i][a];
+        if constexpr (Codec<S>::DARITH) r = p.rref[i] + r;
+        rhof[(long long)i * p.nsites + node] = r;
+        mix += r;
+    }
+    rhof[(long long)NS * p.nsites + node] = mix;
+}
+
+// Isotropic lattice gradient (1/cs0^2) sum_a w_a e_a phi(node + e_a) of a
+// node field (cs0^2 = 1/3); a neighbour beyond a wall (in any component)
+// takes the node's own value, periodic faces wrap.
+template <int LAT, typename T>
+__device__ __forceinline__ void lattice_grad(const Params<T>& p, const Nbr& nb, const T* __restrict__ phi, int node,
+                                             T (&gr)[3])
+{
+    const T own = phi[node];
+    gr[0] = gr[1] = gr[2] = (T)0;
+    static_for<1, Lat<LAT>::Q>([&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
+        const bool solid = (ex == -1 && nb.lo[0]) || (ex == 1 && nb.hi[0]) || (ey == -1 && nb.lo[1]) ||
+                           (ey == 1 && nb.hi[1]) || (ez == -1 && nb.lo[2]) || (ez == 1 && nb.hi[2]);
+        const T v = solid ? own : phi[node + nb.off[0][ex + 1] + nb.off[1][ey + 1] + nb.off[2][ez + 1]];
+        const T wv = p.wl[wclass<LAT>(A)] * v;
+        if constexpr (ex != 0) gr[0] += ex * wv;
+        if constexpr (ey != 0) gr[1] += ey * wv;
+        if constexpr (ez != 0) gr[2] += ez * wv;
+    });
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gr[k] *= (T)3;
+}
+
+// The step with the corrective forcing terms p.flags selects (k_step plus
+// the gradients of the densities k_density wrote for f_t).
+template <int LAT, int NS, typename S, typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_step_corr(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
+            double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
+            const double* __restrict__ corr)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    const bool active = node < p.nsites;
+    T f[NS][Q];
+    T gn[3] = {p.g[0], p.g[1], p.g[2]};
+    if (active) node_force(p, node, gn);
+    NodeState<NS, T> s;
+    unsigned err = 0;
+    if (active) {
+        const Nbr nb = neighbours(p, node);
+        gather_all<LAT, NS>(p, fin, node, nb, f);
+        if (corr) add_correction<LAT, NS>(p, corr, f);
+        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        T grad[NS + 1][3];
+#pragma unroll
+        for (int i = 0; i <= NS; ++i) lattice_grad<LAT>(p, nb, p.rhof + (long long)i * p.nsites, node, grad[i]);
+        collide<LAT, NS, Codec<S>::DARITH, true>(p, f, s, gn, grad);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
     }

@@ -33,6 +33,8 @@ struct HostParams {
     double wl[3];
     double ref[MAXS][3];
     const void* kf;          // device [3][nsites] force field in the arithmetic type, or nullptr
+    unsigned flags;          // corrective forcing terms (EVD_FORCE_S_DIFF / _S_P / _S_RHO)
+    const void* rhof;        // device [ns + 1][nsites] densities of f_t for the gradient terms
 };
 
 // Host-side checks and constants shared by the single-lattice context and the
@@ -92,6 +94,16 @@ struct BatchLaunch {
                                cudaStream_t st);
     static cudaError_t init(const BatchArgs& a, const double* x, const double* n, void* fprev, void* fcur,
                             double* part, unsigned* err, cudaStream_t st);
+};
+
+// The D2Q9 step with the corrective forcing terms: a density pre-pass into
+// h.rhof, then the step with the gradient terms (only D2Q9 translation units
+// define these).
+template <int PREC>
+struct CorrLaunch {
+    static cudaError_t density(const HostParams& h, const void* fin, const double* corr, cudaStream_t st);
+    static cudaError_t step(const HostParams& h, const void* fin, void* fout, double* mass_part, unsigned* err,
+                            int flags, const double* corr, cudaStream_t st);
 };
 
 inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + block - 1) / block; }

@@ -87,3 +87,41 @@ cudaError_t dispatch_init(const HostParams& h, const double* x, const double* n,
         return dispatch_step_tma<S>(h, ty, maps, fin, fout, mp, err, flags, corr, lumps, st);         \
     }                                                                                                 \
     }
+
+#define EVD_DEFINE_CORR_LAUNCHERS(PREC, S, T)                                                         \
+    namespace evd {                                                                                   \
+    template <>                                                                                       \
+    cudaError_t CorrLaunch<PREC>::density(const HostParams& h, const void* fin, const double* corr,   \
+                                          cudaStream_t st)                                            \
+    {                                                                                                 \
+        constexpr int LAT = 0;                                                                        \
+        using St = S;                                                                                 \
+        using Tt = T;                                                                                 \
+        const Params<T> p = to_params<T>(h);                                                          \
+        const int grid = grid_blocks(h, BLOCK);                                                       \
+        if (grid == 0) return cudaSuccess;                                                            \
+        EVD_CORR_DISPATCH(k_density, p, (const S*)fin, (T*)h.rhof, corr)                              \
+        return cudaGetLastError();                                                                    \
+    }                                                                                                 \
+    template <>                                                                                       \
+    cudaError_t CorrLaunch<PREC>::step(const HostParams& h, const void* fin, void* fout, double* mp,  \
+                                       unsigned* err, int flags, const double* corr, cudaStream_t st) \
+    {                                                                                                 \
+        constexpr int LAT = 0;                                                                        \
+        using St = S;                                                                                 \
+        using Tt = T;                                                                                 \
+        const Params<T> p = to_params<T>(h);                                                          \
+        const int grid = grid_blocks(h, BLOCK);                                                       \
+        if (grid == 0) return cudaSuccess;                                                            \
+        EVD_CORR_DISPATCH(k_step_corr, p, (const S*)fin, (S*)fout, mp, err, flags, corr)               \
+        return cudaGetLastError();                                                                    \
+    }                                                                                                 \
+    }
+
+#define EVD_CORR_DISPATCH(KERNEL, ...)                                                                \
+    switch (h.ns) {                                                                                   \
+        case 1: KERNEL<LAT, 1, St, Tt><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;                   \
+        case 2: KERNEL<LAT, 2, St, Tt><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;                   \
+        case 3: KERNEL<LAT, 3, St, Tt><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;                   \
+        default: return cudaErrorInvalidValue;                                                        \
+    }

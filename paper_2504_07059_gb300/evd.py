@@ -23,6 +23,7 @@ EVD_FP64, EVD_FP32, EVD_FP16_STORE = 0, 1, 2
 EVD_WALL_XM, EVD_WALL_XP, EVD_WALL_YM, EVD_WALL_YP, EVD_WALL_ZM, EVD_WALL_ZP = (1, 2, 4, 8, 16, 32)
 EVD_MAX_SPECIES = 3
 EVD_KERNEL_AUTO, EVD_KERNEL_GENERAL, EVD_KERNEL_TMA = 0, 1, 2
+EVD_FORCE_S_DIFF, EVD_FORCE_S_P, EVD_FORCE_S_RHO = 1, 2, 4
 
 STATUS_NAMES = {0: "EVD_OK", 1: "EVD_ERR_ARG", 2: "EVD_ERR_CUDA", 3: "EVD_ERR_UNSTABLE",
                 4: "EVD_ERR_TIMEOUT", 5: "EVD_ERR_STATE"}

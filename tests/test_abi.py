@@ -90,3 +90,19 @@ def test_null_batch_calls_fail_cleanly(evd):
     assert L.evd_batch_set_schedule(None, 128, 0) == evd.EVD_ERR_ARG
     assert L.evd_batch_time(None) == -1 and L.evd_batch_launch_count(None) == -1
     assert L.evd_batch_destroy(None) == evd.EVD_OK
+
+
+def test_corrective_forcing_flags_are_checked(evd):
+    sp3 = evd.SpeciesTable([1.0, 2.0], np.full((2, 2), 0.05), 1.0, flags=evd.EVD_FORCE_S_P)
+    g3 = evd.make_grid(evd.EVD_D3Q19, evd.EVD_FP64, (4, 4, 4), 0)
+    with pytest.raises(evd.EVDError) as ei:           # D2Q9 only
+        evd.evd_create(g3, sp3)
+    assert ei.value.status == evd.EVD_ERR_ARG and "D2Q9" in evd.evd_last_error(None)
+    bad = evd.SpeciesTable([1.0, 2.0], np.full((2, 2), 0.05), 1.0, flags=8)
+    g2 = evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP64, (4, 4), 0)
+    with pytest.raises(evd.EVDError):
+        evd.evd_create(g2, bad)
+    arr = (evd.evd_member * 1)(evd.evd_member(4, 4, 1, 0, evd.SpeciesTable([1.0, 2.0], np.full((2, 2), 0.05), 1.0,
+                                                                           flags=evd.EVD_FORCE_S_DIFF).struct))
+    with pytest.raises(evd.EVDError):
+        evd.evd_batch_create(evd.EVD_D2Q9, evd.EVD_FP64, arr)
