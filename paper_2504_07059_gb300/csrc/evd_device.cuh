@@ -825,9 +825,10 @@ k_step_corr(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
         gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
         moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
-        T grad[NS + 1][3];
+        T grad[NS + 1][3] = {};
+        if (p.rhof)   // only the gradient terms (S_p, S_rho) have a density field
 #pragma unroll
-        for (int i = 0; i <= NS; ++i) lattice_grad<LAT>(p, nb, p.rhof + (long long)i * p.nsites, node, grad[i]);
+            for (int i = 0; i <= NS; ++i) lattice_grad<LAT>(p, nb, p.rhof + (long long)i * p.nsites, node, grad[i]);
         collide<LAT, NS, Codec<S>::DARITH, true>(p, f, s, gn, grad);
         store_all<LAT, NS>(p, fout, node, f, s.rho);
         if (err) atomicOr(err_flag, err);
