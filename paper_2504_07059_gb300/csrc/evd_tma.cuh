@@ -65,6 +65,7 @@ __host__ __device__ constexpr int grp_planes(int g) { return g == 7 ? 1 : grp_si
 template <int NS, typename S, int TY, int SLOTS>
 struct TmaLayout {
     static constexpr int XP = TmaPad<S>::XP;
+    static constexpr int threads = TTX * TY * NS;
     static constexpr bool LOCAL = Codec<S>::LOCAL;
     static constexpr int NG = LOCAL ? NGRP + 1 : NGRP;
     static __host__ __device__ constexpr int bw(int cls) { return (cls & 1) ? TTX + 2 * XP : TTX; }
@@ -90,10 +91,14 @@ struct TmaLayout {
     }
     static constexpr int ring_bytes = SLOTS * slot_bytes;
     static constexpr int exch_bytes = 2 * NS * TY * TTX * 16;   // two float4 buffers
-    static constexpr int msum_offset = ring_bytes + exch_bytes;
+    // float storage: wall populations of the node land here by cp.async
+    // ([direction][thread] words) instead of in registers
+    static constexpr bool CEN_SMEM = sizeof(S) == 4;
+    static constexpr int cen_offset = ring_bytes + exch_bytes;
+    static constexpr int cen_bytes = CEN_SMEM ? 19 * threads * 4 : 0;
+    static constexpr int msum_offset = cen_offset + cen_bytes;
     static constexpr int bar_offset = msum_offset + NS * TY * 8 + 8;
     static constexpr int total_bytes = bar_offset + SLOTS * 8 + 128;   // + alignment slack
-    static constexpr int threads = TTX * TY * NS;
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -140,6 +145,14 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
         "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
+
+// 4-byte global -> shared copy that holds no register while in flight
+__device__ __forceinline__ void cp_async4(unsigned dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
@@ -266,6 +279,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     double* msum = reinterpret_cast<double*>(smem + G::msum_offset);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + G::bar_offset);
     const unsigned ring = smem_u32(smem);
+    const unsigned cen_s = smem_u32(smem + G::cen_offset);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -351,10 +365,17 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const bool wall_node = emit && active && (col_wall || zlo || zhi);
         float f[Q], cen[Q], cenr = 0.0f;
         if (wall_node) {
-            // the node's own post-collision populations, for the App. A terms
+            // the node's own post-collision populations, for the App. A terms:
+            // float storage copies them to shared memory without holding
+            // registers (waited for just before the lumps), half storage
+            // loads them into registers
             static_for<1, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                cen[A] = (float)fin[plane_of<1, NS>(sp, A) * pstride + node];
+                if constexpr (G::CEN_SMEM)
+                    cp_async4(cen_s + (unsigned)((A * G::threads + threadIdx.x) * 4),
+                              fin + (plane_of<1, NS>(sp, A) * pstride + node));
+                else
+                    cen[A] = (float)fin[plane_of<1, NS>(sp, A) * pstride + node];
             });
             if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
         }
@@ -399,6 +420,8 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float rho = 1.0f, drho = 0.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
         if (ok && emit) {
             if (wall_node) {
+                if constexpr (G::CEN_SMEM) cp_async_wait_all();
+                const float* cs = reinterpret_cast<const float*>(smem + G::cen_offset) + threadIdx.x;
                 const float4* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
                 static_for<1, Q>([&](auto ac) {
                     constexpr int A = decltype(ac)::value;
@@ -408,7 +431,10 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                         const float wa = p.wl[wclass<1>(A)];
                         f[A] += l.x * fmaf(wa, cenr, cen[A]) + l.y * fmaf(wa, cenr, cen[AB]);
                     } else {   // deviations, plus the reference the weights carry
-                        f[A] += l.x * cen[A] + l.y * cen[AB] + p.ref[sp][wclass<1>(A)] * l.z;
+                        float ca, cb;
+                        if constexpr (G::CEN_SMEM) { ca = cs[A * G::threads]; cb = cs[AB * G::threads]; }
+                        else { ca = cen[A]; cb = cen[AB]; }
+                        f[A] += l.x * ca + l.y * cb + p.ref[sp][wclass<1>(A)] * l.z;
                     }
                 });
             }

@@ -10,7 +10,9 @@ template <int NS, typename S, int TY>
 cudaError_t launch_tma_ns(const HostParams& h, const TmaMaps& maps, const void* fin, void* fout, double* mp,
                           unsigned* err, int flags, const double* corr, const float* lumps, cudaStream_t st)
 {
-    constexpr int SLOTS = TmaLaunch::SLOTS;
+    // float storage keeps the wall populations in shared memory (cp.async):
+    // three ring slots leave room for them at two CTAs per SM
+    constexpr int SLOTS = sizeof(S) == 4 ? 3 : TmaLaunch::SLOTS;
     using L = TmaLayout<NS, S, TY, SLOTS>;
     auto kern = k_step_tma<NS, S, TY, SLOTS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::total_bytes);
