@@ -225,6 +225,27 @@ int evd_get_kernel(const evd_ctx* ctx);
  * returns EVD_ERR_ARG.  Synchronises. */
 evd_status evd_set_force_field(evd_ctx* ctx, const double* k_host);
 
+/* Discrete adjoint of the step (D2Q9, FP64 storage, uniform g, no corrective
+ * terms, mass correction off; EVD_ERR_ARG otherwise).  From the initial
+ * state x0 (host [ns][sites] mole fractions) and n0 (host [sites] or NULL,
+ * as evd_set_fields), runs nsteps steps and returns the loss
+ *   L = sum_i sum_y (xbar_i(y) - target_i(y))^2,
+ * xbar_i(y) the mean over x of the mole fractions after nsteps steps,
+ * target host [ns][ny]; and its exact gradient with respect to the
+ * Maxwell-Stefan diffusivities (dL_dD host [ns][ns], symmetric, zero
+ * diagonal; NULL to skip) and the body force (dL_dg host [3], z entry 0;
+ * NULL to skip).  The reverse sweep applies the transpose of each step:
+ * the node-local collision's Jacobian (exact, from forward-mode dual numbers
+ * through the collision of Eq. LBE_forcing with tau_ij of Eq.
+ * relation_tauij_diff_coeff) and the transposed gather (Eq.
+ * Second_order_spatial_interpolation and App. A).  States are recomputed from
+ * checkpoints stored every checkpoint_every steps (0: about sqrt(nsteps));
+ * memory: (nsteps / checkpoint_every + checkpoint_every + 3) population
+ * buffers.  Leaves the context at t = nsteps of this run.  Synchronises. */
+evd_status evd_loss_gradient(evd_ctx* ctx, const double* x0, const double* n0, long long nsteps,
+                             const double* target, int checkpoint_every, double* loss, double* dL_dD,
+                             double* dL_dg);
+
 /* Rows per tile of the TMA-staged step: 2 (the default; two CTAs of 6 warps
  * per SM for three species) or 4 (one CTA of 12 warps per SM).  Same results;
  * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not

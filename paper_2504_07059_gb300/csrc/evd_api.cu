@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -981,6 +982,139 @@ evd_status evd_get_target_mass(evd_ctx* c, double* m_host)
     DeviceGuard dg(c->device);
     CK(c, cudaMemcpyAsync(m_host, c->m_target, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    return EVD_OK;
+}
+
+namespace {
+
+// Device buffers released together on every exit path.
+struct DevBufs {
+    std::vector<void*> p;
+    ~DevBufs()
+    {
+        for (void* q : p) cudaFree(q);
+    }
+    cudaError_t alloc(size_t bytes, void** out)
+    {
+        *out = nullptr;
+        cudaError_t e = cudaMalloc(out, bytes);
+        if (e == cudaSuccess) p.push_back(*out);
+        return e;
+    }
+};
+
+}  // namespace
+
+evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, long long nsteps, const double* target,
+                             int checkpoint_every, double* loss, double* dL_dD, double* dL_dg)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (!x0 || !target || !loss) return fail(c, EVD_ERR_ARG, "x0, target and loss must not be NULL");
+    if (c->lattice != EVD_D2Q9 || c->precision != EVD_FP64)
+        return fail(c, EVD_ERR_ARG, "the adjoint is implemented for D2Q9 with FP64 storage");
+    if (c->kf || c->hp.flags || c->mc_every)
+        return fail(c, EVD_ERR_ARG, "the adjoint takes a uniform g, no corrective terms, no mass correction");
+    if (nsteps < 1) return fail(c, EVD_ERR_ARG, "nsteps must be >= 1");
+    if (checkpoint_every < 0) return fail(c, EVD_ERR_ARG, "checkpoint_every must be >= 0");
+    const long long N = nsteps;
+    long long K = checkpoint_every;
+    if (K == 0) {   // about sqrt(N) checkpoints of about sqrt(N) steps each
+        K = 1;
+        while (K * K < N) ++K;
+    }
+    if (K > N) K = N;
+    evd_status s = evd_set_fields(c, x0, n0);
+    if (s != EVD_OK) return s;
+    DeviceGuard dg(c->device);
+    const size_t bb = c->buf_bytes;
+    const size_t n = (size_t)c->nsites;
+    const int np = evd::AdjLaunch::nparams(c->ns);
+    const long long ncp = (N - 1) / K + 1;          // checkpoints f*_0, f*_K, ...
+    DevBufs mem;
+    void *f0 = nullptr, *lam_f = nullptr, *lam_s = nullptr, *xd = nullptr, *nd = nullptr, *dldx = nullptr,
+         *part = nullptr, *grad = nullptr;
+    CK(c, mem.alloc(bb, &f0));
+    CK(c, mem.alloc(bb, &lam_f));
+    CK(c, mem.alloc(bb, &lam_s));
+    CK(c, mem.alloc(c->ns * n * sizeof(double), &xd));
+    if (n0) CK(c, mem.alloc(n * sizeof(double), &nd));
+    CK(c, mem.alloc(c->ns * n * sizeof(double), &dldx));
+    CK(c, mem.alloc((size_t)evd::AdjLaunch::nblocks(c->hp) * np * sizeof(double), &part));
+    CK(c, mem.alloc(np * sizeof(double), &grad));
+    std::vector<void*> cp(ncp, nullptr), seg(K, nullptr);
+    for (auto& q : cp) CK(c, mem.alloc(bb, &q));
+    for (auto& q : seg) CK(c, mem.alloc(bb, &q));
+    cudaStream_t st = c->stream;
+    CK(c, cudaMemcpyAsync(xd, x0, c->ns * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (n0) CK(c, cudaMemcpyAsync(nd, n0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemsetAsync(grad, 0, np * sizeof(double), st));
+    // forward: f_0 and the checkpoints, then N steps to the state the loss reads
+    CK(c, cudaMemcpyAsync(f0, c->buf[c->cur ^ 1], bb, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(cp[0], c->buf[c->cur], bb, cudaMemcpyDeviceToDevice, st));
+    for (long long t = 1; t <= N; ++t) {
+        s = evd_step(c, 1);
+        if (s != EVD_OK) return s;
+        if (t < N && t % K == 0) CK(c, cudaMemcpyAsync(cp[t / K], c->buf[c->cur], bb, cudaMemcpyDeviceToDevice, st));
+    }
+    // the loss: row averages of the mole fractions of f_N against the target
+    std::vector<double> x(c->ns * n), g(c->ns * n, 0.0);
+    s = readout_to_host(c, x.data(), nullptr, nullptr, nullptr);
+    if (s != EVD_OK) return s;
+    double L = 0.0;
+    for (int i = 0; i < c->ns; ++i)
+        for (int y = 0; y < c->ny; ++y) {
+            double m = 0.0;
+            for (int xx = 0; xx < c->nx; ++xx) m += x[(size_t)i * n + (size_t)y * c->nx + xx];
+            m /= c->nx;
+            const double r = m - target[(size_t)i * c->ny + y];
+            L += r * r;
+            for (int xx = 0; xx < c->nx; ++xx) g[(size_t)i * n + (size_t)y * c->nx + xx] = 2.0 * r / c->nx;
+        }
+    *loss = L;
+    CK(c, cudaMemcpyAsync(dldx, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // reverse sweep: lambda_N, then lambda*_{N-1} = G^T lambda_N
+    const HostParams& h = c->hp;
+    c->launches += 2;
+    CK(c, evd::AdjLaunch::readout(h, (const double*)c->buf[c->cur ^ 1], (const double*)dldx, (double*)lam_f, st));
+    CK(c, evd::AdjLaunch::gather_t(h, (const double*)lam_f, (double*)lam_s, st));
+    long long seg_id = -1;
+    for (long long t = N - 1; t >= 1; --t) {
+        // f*_{t-1}, recomputed from its checkpoint with the rest of its segment
+        const long long j = (t - 1) / K;
+        if (j != seg_id) {
+            CK(c, cudaMemcpyAsync(seg[0], cp[j], bb, cudaMemcpyDeviceToDevice, st));
+            const long long last = std::min(j * K + K - 1, N - 2);
+            for (long long q = 1; q <= last - j * K; ++q) CK(c, launch_step(c, seg[q - 1], seg[q], 0, nullptr));
+            seg_id = j;
+        }
+        const double* fprev = (const double*)seg[(t - 1) - j * K];
+        c->launches += 3;
+        CK(c, evd::AdjLaunch::collide(h, fprev, false, (const double*)lam_s, (double*)lam_f, (double*)part,
+                                      (double*)grad, st));
+        CK(c, evd::AdjLaunch::gather_t(h, (const double*)lam_f, (double*)lam_s, st));
+    }
+    // t = 0: f*_0 = C(f_0), and f_0 itself depends on g
+    c->launches += 4;
+    CK(c, evd::AdjLaunch::collide(h, (const double*)f0, true, (const double*)lam_s, (double*)lam_f, (double*)part,
+                                  (double*)grad, st));
+    CK(c, evd::AdjLaunch::init_g(h, (const double*)xd, (const double*)nd, (const double*)lam_f, (double*)part,
+                                 (double*)grad, st));
+    std::vector<double> gr(np);
+    CK(c, cudaMemcpyAsync(gr.data(), grad, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    s = evd_check(c);
+    if (s != EVD_OK) return s;
+    if (dL_dD) {
+        for (int q = 0; q < c->ns * c->ns; ++q) dL_dD[q] = 0.0;
+        int m = 0;
+        for (int i = 0; i < c->ns; ++i)
+            for (int k = i + 1; k < c->ns; ++k, ++m) dL_dD[i * c->ns + k] = dL_dD[k * c->ns + i] = gr[m];
+    }
+    if (dL_dg) {
+        dL_dg[0] = gr[np - 2];
+        dL_dg[1] = gr[np - 1];
+        dL_dg[2] = 0.0;
+    }
     return EVD_OK;
 }
 

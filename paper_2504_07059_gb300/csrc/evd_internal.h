@@ -106,6 +106,22 @@ struct CorrLaunch {
                             int flags, const double* corr, cudaStream_t st);
 };
 
+// Kernels of the discrete adjoint (D2Q9, FP64): lambda_t = C^T lambda*_t with
+// the parameter gradient accumulated into grad[nparams] (D_ij for i < j, then
+// g_x, g_y); lambda*_{t-1} = G^T lambda_t; the readout and initial-state
+// terms.  part: scratch of nblocks * nparams doubles.
+struct AdjLaunch {
+    static int nparams(int ns);
+    static int nblocks(const HostParams& h);
+    static cudaError_t collide(const HostParams& h, const double* fin, bool raw, const double* lam_star,
+                               double* lam_f, double* part, double* grad, cudaStream_t st);
+    static cudaError_t gather_t(const HostParams& h, const double* lam_f, double* lam_star, cudaStream_t st);
+    static cudaError_t readout(const HostParams& h, const double* fin, const double* dldx, double* lam_f,
+                               cudaStream_t st);
+    static cudaError_t init_g(const HostParams& h, const double* x0, const double* n0, const double* lam0,
+                              double* part, double* grad, cudaStream_t st);
+};
+
 inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + block - 1) / block; }
 
 // The D3Q19 step with TMA-staged tiles (float and half storage only).

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "evd_get_kernel": (ctypes.c_int, [_vp]),
     "evd_set_tile_rows": (_st, [_vp, ctypes.c_int]),
     "evd_set_force_field": (_st, [_vp, _vp]),
+    "evd_loss_gradient": (_st, [_vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
@@ -293,6 +294,18 @@ def evd_get_kernel(ctx) -> int:
 def evd_set_force_field(ctx, k=None):
     """k: [D][sites] float64 (host), or None to remove the field."""
     _check(lib().evd_set_force_field(ctx, _ptr(k)), ctx)
+
+
+def evd_loss_gradient(ctx, x0, target, nsteps: int, n0=None, checkpoint_every: int = 0):
+    """(loss, dL/dD [ns][ns], dL/dg [3]) of the mole-fraction misfit after
+    nsteps steps from x0 (evd_loss_gradient)."""
+    ns = target.shape[0]
+    loss = np.zeros(1)
+    dD = np.zeros(ns * ns)
+    dg = np.zeros(3)
+    _check(lib().evd_loss_gradient(ctx, _ptr(x0), _ptr(n0), int(nsteps), _ptr(target), int(checkpoint_every),
+                                   loss.ctypes.data, dD.ctypes.data, dg.ctypes.data), ctx)
+    return float(loss[0]), dD.reshape(ns, ns), dg
 
 
 def evd_set_tile_rows(ctx, rows: int):
