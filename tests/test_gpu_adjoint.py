@@ -1,0 +1,102 @@
+"""The discrete adjoint (evd_loss_gradient, D2Q9 FP64) against central finite
+differences of the FP64 oracle's own loss (independent code), the loss itself
+against the oracle, checkpoint invariance, and the torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_07059_gb300 import adjoint as ADJ
+from paper_2504_07059_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_loss(prob: ADJ.Problem, d_pairs, g):
+    ns = len(prob.molar_mass)
+    o = O.Oracle(W.D2Q9, prob.shape, prob.wall_mask, prob.molar_mass, ADJ.pairs_to_matrix(ns, d_pairs),
+                 prob.tau1, (g[0], g[1]))
+    o.init(prob.x0, prob.n0)
+    o.step(prob.nsteps)
+    xbar = o.observables()["x"][:, 0].mean(axis=2)
+    return float(((xbar - prob.target) ** 2).sum())
+
+
+def make_problem(shape, walls, M, d_pairs, g, steps, stream):
+    """A seeded mixture and a target profile: the oracle's row averages after
+    the same number of steps with every parameter perturbed (the recipe of the
+    inverse problem: D x 1.1, g x 0.9)."""
+    wl = W.random_mixture(W.D2Q9, shape, walls, M, stream=stream)
+    prob = ADJ.Problem(shape, walls, tuple(M), 1.0, wl.x, np.zeros((len(M), shape[1])), steps)
+    ns = len(M)
+    o = O.Oracle(W.D2Q9, shape, walls, M, ADJ.pairs_to_matrix(ns, 1.1 * np.asarray(d_pairs)), 1.0,
+                 (0.9 * g[0], 0.9 * g[1]))
+    o.init(wl.x)
+    o.step(steps)
+    prob.target = o.observables()["x"][:, 0].mean(axis=2)
+    return prob
+
+
+CASES = {
+    "ternary-walls-y": (lambda: make_problem((10, 24), W.WALL_Y, (1.0, 3.0, 7.0), (0.06, 0.08, 0.07),
+                                             (2e-6, -1e-5), 40, 1400), (0.06, 0.08, 0.07), (2e-6, -1e-5)),
+    "binary-closed-box": (lambda: make_problem((8, 12), W.WALL_X | W.WALL_Y, (1.0, 2.5), (0.05,),
+                                               (1e-5, -2e-5), 30, 1410), (0.05,), (1e-5, -2e-5)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_gradient_matches_central_differences_of_the_oracle(evd, name):
+    make, d, g = CASES[name]
+    prob = make()
+    loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
+    L0 = oracle_loss(prob, d, g)
+    assert abs(loss - L0) <= 1e-10 * abs(L0), (loss, L0)
+    theta = np.array(list(d) + list(g))
+    adj = np.concatenate([dd, dg])
+    fd = np.zeros_like(theta)
+    for k in range(len(theta)):
+        h = 1e-4 * abs(theta[k])
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        nd = len(d)
+        fd[k] = (oracle_loss(prob, tp[:nd], tp[nd:]) - oracle_loss(prob, tm[:nd], tm[nd:])) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    for k in range(len(theta)):
+        assert abs(adj[k] - fd[k]) <= 1e-4 * max(abs(fd[k]), 1e-3 * scale), (k, adj, fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(evd):
+    make, d, g = CASES["ternary-walls-y"]
+    prob = make()
+    results = []
+    for k in (1, 0, 7, prob.nsteps):
+        prob.checkpoint_every = k
+        results.append(ADJ.loss_and_gradient(prob, d, g))
+    for r in results[1:]:
+        assert r[0] == results[0][0]
+        assert np.array_equal(r[1], results[0][1]) and np.array_equal(r[2], results[0][2])
+
+
+def test_torch_autograd_function_returns_the_adjoint_gradient(evd):
+    import torch
+    make, d, g = CASES["binary-closed-box"]
+    prob = make()
+    dt = torch.tensor(d, dtype=torch.float64, requires_grad=True)
+    gt = torch.tensor(g, dtype=torch.float64, requires_grad=True)
+    loss = ADJ.MoleFractionMisfit.apply(dt, gt, prob)
+    (2.0 * loss).backward()
+    ref = ADJ.loss_and_gradient(prob, d, g)
+    assert float(loss.detach()) == ref[0]
+    assert np.allclose(dt.grad.numpy(), 2.0 * ref[1], rtol=0, atol=0)
+    assert np.allclose(gt.grad.numpy(), 2.0 * ref[2], rtol=0, atol=0)
+
+
+def test_adjoint_rejects_what_it_does_not_cover(evd):
+    wl = W.random_mixture(W.D2Q9, (6, 6), W.WALL_Y, (1.0, 2.0), stream=1420)
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp32")
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_loss_gradient(sim.ctx, wl.x, np.zeros((2, 6)), 5)
+    assert ei.value.status == evd.EVD_ERR_ARG
+    sim.close()
