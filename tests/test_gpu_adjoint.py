@@ -46,6 +46,12 @@ CASES = {
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_adjoint_gradient_matches_central_differences_of_the_oracle(evd, name):
+    """Every component within 1e-4 relative of the oracle's finite differences:
+    central differences with h = 1e-4 |theta_k| for the diffusivities
+    (observed 7e-8 to 1e-7: the h^2 truncation); for the body force, whose
+    loss derivative can be small enough that differences at that step are
+    roundoff-limited, a fourth-order difference with h = 1e-2 |g_k| (observed
+    <= 4e-6)."""
     make, d, g = CASES[name]
     prob = make()
     loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
@@ -53,18 +59,20 @@ def test_adjoint_gradient_matches_central_differences_of_the_oracle(evd, name):
     assert abs(loss - L0) <= 1e-10 * abs(L0), (loss, L0)
     theta = np.array(list(d) + list(g))
     adj = np.concatenate([dd, dg])
+    nd = len(d)
+    L = lambda t: oracle_loss(prob, t[:nd], t[nd:])
     fd = np.zeros_like(theta)
     for k in range(len(theta)):
-        h = 1e-4 * abs(theta[k])
-        tp, tm = theta.copy(), theta.copy()
-        tp[k] += h
-        tm[k] -= h
-        nd = len(d)
-        fd[k] = (oracle_loss(prob, tp[:nd], tp[nd:]) - oracle_loss(prob, tm[:nd], tm[nd:])) / (2 * h)
-    scale = np.abs(fd).max()
-    assert scale > 0
-    for k in range(len(theta)):
-        assert abs(adj[k] - fd[k]) <= 1e-4 * max(abs(fd[k]), 1e-3 * scale), (k, adj, fd)
+        e = np.zeros_like(theta)
+        if k < nd:
+            e[k] = 1e-4 * abs(theta[k])
+            fd[k] = (L(theta + e) - L(theta - e)) / (2 * e[k])
+        else:
+            e[k] = 1e-2 * abs(theta[k])
+            fd[k] = (8 * (L(theta + e) - L(theta - e)) - (L(theta + 2 * e) - L(theta - 2 * e))) / (12 * e[k])
+    assert np.all(np.abs(fd) > 0)
+    rel = np.abs(adj - fd) / np.abs(fd)
+    assert rel.max() < 1e-4, (rel, adj, fd)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(evd):
