@@ -43,20 +43,27 @@ UNIT = "GLUPS"
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel launch, keyed
-# by (kernel source digest, workload, cube side, precision), from an ncu
-# capture of the kernel source with this digest (summaries under profiles/).  A kernel
+# by (digest of KERNEL_SOURCES, workload, cube side, precision), from an ncu
+# capture of the kernel sources with this digest (summaries under profiles/).
+# A change to those sources changes the digest and the entry no longer applies.  A kernel
 # change changes the digest and the entry no longer applies.
 NCU_TRAFFIC = {
     # 128^3 capture: 547.3 MB read + 438.3 MB written; x8 for a 256^3 launch
-    ("e54fa6f9be2832d2", "stratification", 256, "fp32"): 7884.9e6,
+    ("01e60b946a78549c", "stratification", 256, "fp32"): 7884.9e6,
 }
+
+
+# The sources that define the step kernels and their launch configuration
+# (the device code, the TMA step, the launchers and the FP32/FP16 D3Q19 units).
+KERNEL_SOURCES = ("evd_device.cuh", "evd_tma.cuh", "evd_tma_launch.cuh", "evd_launch.cuh",
+                  "evd_fp32_d3q19.cu", "evd_fp16_d3q19.cu")
 
 
 def kernel_digest() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2504_07059_gb300", "csrc", "*"))):
-        with open(p, "rb") as fh:
-            h.update(os.path.basename(p).encode())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2504_07059_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
