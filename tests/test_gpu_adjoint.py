@@ -1,9 +1,12 @@
-"""The discrete adjoint (evd_loss_gradient, D2Q9 FP64) against central finite
-differences of the FP64 oracle's own loss (independent code), the loss itself
-against the oracle, checkpoint invariance, and the torch.autograd wrapper."""
+"""The discrete adjoint (evd_loss_gradient, D2Q9 FP64) against the oracle's
+own discrete adjoint (reverse mode through the oracle's map) and against
+central finite differences of the FP64 oracle's loss (independent code), the
+loss itself against the oracle, checkpoint invariance, and the
+torch.autograd wrapper."""
 import numpy as np
 import pytest
 
+from oracle import discrete_adjoint as DA
 from oracle import oracle as O
 from paper_2504_07059_gb300 import adjoint as ADJ
 from paper_2504_07059_gb300 import workloads as W
@@ -73,6 +76,22 @@ def test_adjoint_gradient_matches_central_differences_of_the_oracle(evd, name):
     assert np.all(np.abs(fd) > 0)
     rel = np.abs(adj - fd) / np.abs(fd)
     assert rel.max() < 1e-4, (rel, adj, fd)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_gradient_matches_the_oracles_discrete_adjoint(evd, name):
+    """Both are the exact gradient of the same discrete map (the CUDA one by
+    dual-number Jacobians and a transposed gather, the oracle's by reverse
+    mode through its tensor restatement), so they differ by rounding only:
+    1e-9 relative per component, 1e-12 on the loss."""
+    make, d, g = CASES[name]
+    prob = make()
+    loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
+    L, odd, odg = DA.loss_and_gradient(prob.shape, prob.wall_mask, prob.molar_mass, prob.tau1, prob.x0,
+                                       prob.target, prob.nsteps, d, g, prob.n0)
+    assert abs(loss - L) <= 1e-12 * L, (loss, L)
+    ours, theirs = np.concatenate([dd, dg]), np.concatenate([odd, odg])
+    assert np.all(np.abs(ours - theirs) <= 1e-9 * np.abs(theirs)), (ours, theirs)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(evd):
