@@ -2,7 +2,7 @@
 """Throughput of the fused EVD lattice Boltzmann step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload stratification|tube] [--precision fp32|fp64|fp16]
+                    [--workload stratification|tube|tubes|adjoint] [--precision fp32|fp64|fp16]
 
 One bench step is one time step of the whole hot path (gather with
 interpolation and wall scheme, moments, tau_ij, collision with forcing) over
@@ -13,6 +13,10 @@ so HBM bandwidth is the bound and no L2 flush is needed between steps), FP32.
 Metric: species-site updates per second, GLUPS = N_species * sites * steps /
 time / 1e9, whole job over all ranks.  Every rank runs an independent replica
 (the path is single-GPU; there is no data-path collective), so scaling is weak.
+
+``--workload adjoint`` times instead the loss and exact gradient of the
+mole-fraction misfit (evd_loss_gradient, FP64) over ``--steps`` steps of the
+128 x 512 ternary D2Q9 tube with gravity of the inverse problem, one GPU.
 
 Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead (the paper publishes no
@@ -45,8 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel launch, keyed
 # by (digest of KERNEL_SOURCES, workload, cube side, precision), from an ncu
 # capture of the kernel sources with this digest (summaries under profiles/).
-# A change to those sources changes the digest and the entry no longer applies.  A kernel
-# change changes the digest and the entry no longer applies.
+# A change to those sources changes the digest and the entry no longer applies.
 NCU_TRAFFIC = {
     # 128^3 capture: 547.3 MB read + 438.3 MB written; x8 for a 256^3 launch
     ("01e60b946a78549c", "stratification", 256, "fp32"): 7884.9e6,
@@ -404,6 +407,65 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
         print(json.dumps(out), flush=True)
 
 
+def run_adjoint(args, torch, dev) -> None:
+    """Loss and gradient per step of the horizon: forward steps with
+    checkpoints, recomputation and the reverse sweep, through the C ABI call
+    (host inputs and outputs, allocations included), for the hand-written
+    reverse sweep and the dual-number cross-check; the FP64 forward step on
+    the same lattice beside them (CUDA events)."""
+    from paper_2504_07059_gb300 import adjoint as ADJ, evd
+    wl = W.loschmidt_ternary_gravity(nx=128, ny=512)
+    nsteps = args.steps
+    d = [wl.D[0, 1], wl.D[0, 2], wl.D[1, 2]]
+    g = (0.0, wl.g[1])
+    stream = torch.cuda.current_stream(dev)
+    # target: the same run with every diffusivity x 1.1 and the force x 0.9
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, 1.1 * wl.D, wl.tau1,
+                         (0.0, 0.9 * wl.g[1]), "fp64", stream)
+    sim.set_fields(wl.x)
+    sim.step(nsteps)
+    target = sim.mole_fractions()[:, 0].mean(axis=2)
+    sim.close()
+    prob = ADJ.Problem(wl.shape[:2], wl.wall_mask, wl.M, wl.tau1, wl.x, target, nsteps)
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp64", stream)
+    sim.set_fields(wl.x)
+    evd.evd_step(sim.ctx, args.warmup)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    evd.evd_step(sim.ctx, nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sim.check()
+    fwd_ms = e0.elapsed_time(e1) / nsteps
+    sim.close()
+    res = {}
+    for name, mode in (("reverse", evd.EVD_ADJOINT_REVERSE), ("dual", evd.EVD_ADJOINT_DUAL)):
+        prob.mode = mode
+        warm = ADJ.Problem(prob.shape, prob.wall_mask, prob.molar_mass, prob.tau1, prob.x0, prob.target,
+                           args.warmup, mode=mode)
+        ADJ.loss_and_gradient(warm, d, g)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
+        res[name] = ((time.perf_counter() - t0) * 1e3 / nsteps, loss, dd, dg)
+    ms = res["reverse"][0]
+    rel = float(np.max(np.abs(np.concatenate(res["reverse"][2:]) - np.concatenate(res["dual"][2:])) /
+                       np.abs(np.concatenate(res["dual"][2:]))))
+    ssu = wl.ns * wl.nsites
+    print(json.dumps({
+        "metric": "adjoint species-site updates/s (GLUPS)", "value": ssu / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": 1, "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "inverse-problem tube 128x512 ternary D2Q9, gravity, loss + gradient "
+                               "w.r.t. 3 D_ij and g", "checkpoint_every": "ceil(sqrt(steps))"},
+        "forward_fp64_ms_per_step": fwd_ms, "reverse_over_forward": ms / fwd_ms,
+        "dual_ms_per_step": res["dual"][0], "reverse_vs_dual_max_rel_diff": rel,
+        "loss": res["reverse"][1], "dL_dD": list(map(float, res["reverse"][2])),
+        "dL_dg": list(map(float, res["reverse"][3])),
+    }), flush=True)
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -418,6 +480,12 @@ def run_ours(args) -> None:
 
     from paper_2504_07059_gb300 import build, evd
     build.build()
+    if args.workload == "adjoint":
+        if rank == 0:
+            run_adjoint(args, torch, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if args.workload == "tubes":
         run_tubes(args, torch, dev, world, rank, local)
         if world > 1:
@@ -549,9 +617,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stratification", "tube", "tubes"], default="stratification",
+    ap.add_argument("--workload", choices=["stratification", "tube", "tubes", "adjoint"], default="stratification",
                     help="stratification: 256^3 D3Q19 closed box; tube: 64x1024 ternary D2Q9 tube; "
-                         "tubes: the batched sweep of 512 D2Q9 tubes")
+                         "tubes: the batched sweep of 512 D2Q9 tubes; adjoint: loss and gradient on the "
+                         "128x512 ternary inverse-problem tube (one GPU)")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16"], default="fp32")
     ap.add_argument("--size", type=int, default=256, help="cube side of the stratification workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")

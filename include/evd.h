@@ -246,6 +246,18 @@ evd_status evd_loss_gradient(evd_ctx* ctx, const double* x0, const double* n0, l
                              const double* target, int checkpoint_every, double* loss, double* dL_dD,
                              double* dL_dg);
 
+/* How evd_loss_gradient applies the transpose of each node's collision
+ * Jacobian.  EVD_ADJOINT_REVERSE (the default): reverse mode written out by
+ * hand through the moments, tau_ij, V_i, the equilibria and the forcing term
+ * of Eq. LBE_forcing (only the small Jacobian of the closed-form tau_ij is
+ * taken in forward mode).  EVD_ADJOINT_DUAL: the Jacobian from forward-mode
+ * dual numbers through the same collision code as the step, one tangent per
+ * node moment (rho_i, J_i) and per parameter; slower, kept as a cross-check.
+ * Both are exact up to rounding.  EVD_ERR_ARG for any other mode. */
+#define EVD_ADJOINT_REVERSE 0
+#define EVD_ADJOINT_DUAL 1
+evd_status evd_set_adjoint_mode(evd_ctx* ctx, int mode);
+
 /* Rows per tile of the TMA-staged step: 2 (the default; two CTAs of 6 warps
  * per SM for three species) or 4 (one CTA of 12 warps per SM).  Same results;
  * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not

@@ -31,6 +31,7 @@ class Problem:
     nsteps: int
     n0: np.ndarray | None = None
     checkpoint_every: int = 0
+    mode: int = 0           # evd.EVD_ADJOINT_REVERSE (default) or evd.EVD_ADJOINT_DUAL
 
 
 def pairs_to_matrix(ns: int, d_pairs) -> np.ndarray:
@@ -53,6 +54,7 @@ def loss_and_gradient(problem: Problem, d_pairs, g):
         x0 = np.ascontiguousarray(problem.x0, dtype=np.float64)
         n0 = None if problem.n0 is None else np.ascontiguousarray(problem.n0, dtype=np.float64)
         tgt = np.ascontiguousarray(problem.target, dtype=np.float64)
+        evd.evd_set_adjoint_mode(sim.ctx, problem.mode)
         loss, dD, dg = evd.evd_loss_gradient(sim.ctx, x0, tgt, problem.nsteps, n0, problem.checkpoint_every)
     finally:
         sim.close()

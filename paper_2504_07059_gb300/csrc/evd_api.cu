@@ -60,6 +60,7 @@ struct evd_ctx {
     int kernel;          // EVD_KERNEL_GENERAL or EVD_KERNEL_TMA
     int tma_blocks;      // grid of the TMA step
     int tma_ty;          // rows per tile of the TMA step (2 or 4)
+    int adj_mode = EVD_ADJOINT_REVERSE;   // how evd_loss_gradient transposes the collision
     int last_parts;      // mass partials written by the last measuring launch
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
@@ -945,6 +946,15 @@ evd_status evd_set_force_field(evd_ctx* c, const double* k_host)
     return EVD_OK;
 }
 
+evd_status evd_set_adjoint_mode(evd_ctx* c, int mode)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (mode != EVD_ADJOINT_REVERSE && mode != EVD_ADJOINT_DUAL)
+        return fail(c, EVD_ERR_ARG, "mode must be EVD_ADJOINT_REVERSE or EVD_ADJOINT_DUAL");
+    c->adj_mode = mode;
+    return EVD_OK;
+}
+
 evd_status evd_set_tile_rows(evd_ctx* c, int rows)
 {
     if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
@@ -1090,13 +1100,13 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
         const double* fprev = (const double*)seg[(t - 1) - j * K];
         c->launches += 3;
         CK(c, evd::AdjLaunch::collide(h, fprev, false, (const double*)lam_s, (double*)lam_f, (double*)part,
-                                      (double*)grad, st));
+                                      (double*)grad, c->adj_mode == EVD_ADJOINT_DUAL, st));
         CK(c, evd::AdjLaunch::gather_t(h, (const double*)lam_f, (double*)lam_s, st));
     }
     // t = 0: f*_0 = C(f_0), and f_0 itself depends on g
     c->launches += 4;
     CK(c, evd::AdjLaunch::collide(h, (const double*)f0, true, (const double*)lam_s, (double*)lam_f, (double*)part,
-                                  (double*)grad, st));
+                                  (double*)grad, c->adj_mode == EVD_ADJOINT_DUAL, st));
     CK(c, evd::AdjLaunch::init_g(h, (const double*)xd, (const double*)nd, (const double*)lam_f, (double*)part,
                                  (double*)grad, st));
     std::vector<double> gr(np);

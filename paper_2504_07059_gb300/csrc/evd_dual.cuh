@@ -6,7 +6,9 @@
 // Dual<N>, with the N tangents seeded on the node's populations and on the
 // parameters, it yields the exact Jacobian of f* at the node, from which the
 // adjoint takes its transpose-vector product.  Only the operations those
-// templates use are provided.
+// templates use are provided.  Loops over the tangents unroll for up to 8
+// tangents (registers) and stay rolled above (the tangents then live in local
+// memory, which keeps compile times reasonable).
 #pragma once
 
 #include <cmath>
@@ -21,7 +23,7 @@ struct Dual {
     Dual() = default;   // trivial (shared-memory tables); Dual(0.0) for a zero
     __host__ __device__ Dual(double x) : v(x)
     {
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) d[k] = 0.0;
     }
     __host__ __device__ explicit operator double() const { return v; }
@@ -29,20 +31,20 @@ struct Dual {
     __host__ __device__ Dual& operator+=(const Dual& b)
     {
         v += b.v;
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) d[k] += b.d[k];
         return *this;
     }
     __host__ __device__ Dual& operator-=(const Dual& b)
     {
         v -= b.v;
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) d[k] -= b.d[k];
         return *this;
     }
     __host__ __device__ Dual& operator*=(const Dual& b)
     {
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) d[k] = d[k] * b.v + v * b.d[k];
         v *= b.v;
         return *this;
@@ -61,7 +63,7 @@ __host__ __device__ inline Dual<N> operator-(const Dual<N>& a)
     Dual<N> r;
     r.v = -a.v;
     
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
     return r;
 }
@@ -73,7 +75,7 @@ __host__ __device__ inline Dual<N> operator/(const Dual<N>& a, const Dual<N>& b)
     r.v = a.v / b.v;
     const double ib = 1.0 / b.v;
     
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
     return r;
 }
@@ -83,7 +85,7 @@ __host__ __device__ inline Dual<N> fma(const Dual<N>& a, const Dual<N>& b, const
     Dual<N> r;
     r.v = a.v * b.v + c.v;
     
-#pragma unroll 1
+#pragma unroll (N <= 8 ? N : 1)
         for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k] + c.d[k];
     return r;
 }

@@ -114,7 +114,7 @@ struct AdjLaunch {
     static int nparams(int ns);
     static int nblocks(const HostParams& h);
     static cudaError_t collide(const HostParams& h, const double* fin, bool raw, const double* lam_star,
-                               double* lam_f, double* part, double* grad, cudaStream_t st);
+                               double* lam_f, double* part, double* grad, bool dual, cudaStream_t st);
     static cudaError_t gather_t(const HostParams& h, const double* lam_f, double* lam_star, cudaStream_t st);
     static cudaError_t readout(const HostParams& h, const double* fin, const double* dldx, double* lam_f,
                                cudaStream_t st);

@@ -23,6 +23,7 @@ EVD_FP64, EVD_FP32, EVD_FP16_STORE = 0, 1, 2
 EVD_WALL_XM, EVD_WALL_XP, EVD_WALL_YM, EVD_WALL_YP, EVD_WALL_ZM, EVD_WALL_ZP = (1, 2, 4, 8, 16, 32)
 EVD_MAX_SPECIES = 3
 EVD_KERNEL_AUTO, EVD_KERNEL_GENERAL, EVD_KERNEL_TMA = 0, 1, 2
+EVD_ADJOINT_REVERSE, EVD_ADJOINT_DUAL = 0, 1
 EVD_FORCE_S_DIFF, EVD_FORCE_S_P, EVD_FORCE_S_RHO = 1, 2, 4
 
 STATUS_NAMES = {0: "EVD_OK", 1: "EVD_ERR_ARG", 2: "EVD_ERR_CUDA", 3: "EVD_ERR_UNSTABLE",
@@ -84,6 +85,7 @@ _SIGNATURES = {
     "evd_set_kernel": (_st, [_vp, ctypes.c_int]),
     "evd_get_kernel": (ctypes.c_int, [_vp]),
     "evd_set_tile_rows": (_st, [_vp, ctypes.c_int]),
+    "evd_set_adjoint_mode": (_st, [_vp, ctypes.c_int]),
     "evd_set_force_field": (_st, [_vp, _vp]),
     "evd_loss_gradient": (_st, [_vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
@@ -306,6 +308,10 @@ def evd_loss_gradient(ctx, x0, target, nsteps: int, n0=None, checkpoint_every: i
     _check(lib().evd_loss_gradient(ctx, _ptr(x0), _ptr(n0), int(nsteps), _ptr(target), int(checkpoint_every),
                                    loss.ctypes.data, dD.ctypes.data, dg.ctypes.data), ctx)
     return float(loss[0]), dD.reshape(ns, ns), dg
+
+
+def evd_set_adjoint_mode(ctx, mode: int):
+    _check(lib().evd_set_adjoint_mode(ctx, int(mode)), ctx)
 
 
 def evd_set_tile_rows(ctx, rows: int):

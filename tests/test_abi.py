@@ -67,6 +67,7 @@ def test_null_context_calls_fail_cleanly(evd):
     assert L.evd_time(None) == -1
     assert L.evd_launch_count(None) == -1
     assert L.evd_set_mass_correction(None, 4) == evd.EVD_ERR_ARG
+    assert L.evd_set_adjoint_mode(None, evd.EVD_ADJOINT_DUAL) == evd.EVD_ERR_ARG
 
 
 def test_batch_rejects_invalid_members_before_any_cuda_call(evd):

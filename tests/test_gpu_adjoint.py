@@ -78,20 +78,38 @@ def test_adjoint_gradient_matches_central_differences_of_the_oracle(evd, name):
     assert rel.max() < 1e-4, (rel, adj, fd)
 
 
+@pytest.mark.parametrize("mode", ["reverse", "dual"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_gradient_matches_the_oracles_discrete_adjoint(evd, name):
+def test_adjoint_gradient_matches_the_oracles_discrete_adjoint(evd, name, mode):
     """Both are the exact gradient of the same discrete map (the CUDA one by
-    dual-number Jacobians and a transposed gather, the oracle's by reverse
-    mode through its tensor restatement), so they differ by rounding only:
-    1e-9 relative per component, 1e-12 on the loss."""
+    a hand-written reverse sweep, or dual-number Jacobians, and a transposed
+    gather; the oracle's by reverse mode through its tensor restatement), so
+    they differ by rounding only: 1e-9 relative per component, 1e-12 on the
+    loss."""
     make, d, g = CASES[name]
     prob = make()
+    prob.mode = evd.EVD_ADJOINT_REVERSE if mode == "reverse" else evd.EVD_ADJOINT_DUAL
     loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
     L, odd, odg = DA.loss_and_gradient(prob.shape, prob.wall_mask, prob.molar_mass, prob.tau1, prob.x0,
                                        prob.target, prob.nsteps, d, g, prob.n0)
     assert abs(loss - L) <= 1e-12 * L, (loss, L)
     ours, theirs = np.concatenate([dd, dg]), np.concatenate([odd, odg])
     assert np.all(np.abs(ours - theirs) <= 1e-9 * np.abs(theirs)), (ours, theirs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_reverse_and_dual_modes_agree(evd, name):
+    """The hand-written reverse sweep against the dual-number Jacobian of the
+    step's own collision code: the same products, summed in another order."""
+    make, d, g = CASES[name]
+    prob = make()
+    out = []
+    for mode in (evd.EVD_ADJOINT_REVERSE, evd.EVD_ADJOINT_DUAL):
+        prob.mode = mode
+        out.append(ADJ.loss_and_gradient(prob, d, g))
+    assert out[0][0] == out[1][0]
+    a, b = np.concatenate(out[0][1:]), np.concatenate(out[1][1:])
+    assert np.all(np.abs(a - b) <= 1e-12 * np.abs(b)), (a, b)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(evd):
@@ -125,5 +143,8 @@ def test_adjoint_rejects_what_it_does_not_cover(evd):
     sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp32")
     with pytest.raises(evd.EVDError) as ei:
         evd.evd_loss_gradient(sim.ctx, wl.x, np.zeros((2, 6)), 5)
+    assert ei.value.status == evd.EVD_ERR_ARG
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_set_adjoint_mode(sim.ctx, 7)
     assert ei.value.status == evd.EVD_ERR_ARG
     sim.close()
