@@ -100,7 +100,10 @@ def test_adjoint_gradient_matches_the_oracles_discrete_adjoint(evd, name, mode):
 @pytest.mark.parametrize("name", list(CASES))
 def test_reverse_and_dual_modes_agree(evd, name):
     """The hand-written reverse sweep against the dual-number Jacobian of the
-    step's own collision code: the same products, summed in another order."""
+    step's own collision code: the same products, summed in another order.
+    Normwise, to 1e-12 of the largest component: a component that is small
+    through cancellation (g_x here, 3e-4 of the largest) carries the rounding
+    of the large terms it cancels (observed 4.6e-12 of itself)."""
     make, d, g = CASES[name]
     prob = make()
     out = []
@@ -109,7 +112,7 @@ def test_reverse_and_dual_modes_agree(evd, name):
         out.append(ADJ.loss_and_gradient(prob, d, g))
     assert out[0][0] == out[1][0]
     a, b = np.concatenate(out[0][1:]), np.concatenate(out[1][1:])
-    assert np.all(np.abs(a - b) <= 1e-12 * np.abs(b)), (a, b)
+    assert np.all(np.abs(a - b) <= 1e-12 * np.abs(b).max()), (a, b)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(evd):
