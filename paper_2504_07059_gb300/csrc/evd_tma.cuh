@@ -192,14 +192,45 @@ __device__ __forceinline__ MaskedW masked_weights(const float (&w)[3], bool lo, 
     return m;
 }
 
+// Half storage: the stored densities rho~ of the 3x3 in-plane neighbourhood of
+// the thread's node in this stage (group 7, which carries the x and y halo).
+template <int NS, typename S, int TY, int SLOTS>
+__device__ __forceinline__ void dens_block(const unsigned char* slot, int sp, int tx, int ty, float (&rd)[3][3])
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    constexpr int W7 = G::bw(3);
+    const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) rd[oy][ox] = (float)r[(ty + oy) * W7 + tx + G::XP - 1 + ox];
+}
+
+// rho~ interpolated with the in-plane stencil (and masked weights) of the
+// directions whose in-plane components are (ex, ey).  A half population is
+// g + w_a rho~ at every stencil node, so by linearity its interpolant is the
+// interpolant of g plus w_a times this one, which every direction with the
+// same (ex, ey) shares (up to three in D3Q19).
+template <int ex, int ey>
+__device__ __forceinline__ float dens_interp(const float (&rd)[3][3], const MaskedW& mx, const MaskedW& my)
+{
+    constexpr int xi = ex > 0 ? 0 : 1, yi = ey > 0 ? 0 : 1;
+    auto row = [&](int oy) -> float {
+        if constexpr (ex == 0) return rd[oy][1];
+        else return mx.w[xi][0] * rd[oy][0] + mx.w[xi][1] * rd[oy][1] + mx.w[xi][2] * rd[oy][2];
+    };
+    if constexpr (ey == 0) return row(1);
+    else return my.w[yi][0] * row(0) + my.w[yi][1] * row(1) + my.w[yi][2] * row(2);
+}
+
 // In-plane interpolation of direction A: float storage interpolates the
 // deviations from its reference as they are (the reference carried by the
-// weights is added at wall nodes only, through K - 1); half storage decodes
-// every stencil value with the density rho~ stored for that node (group 7 of
-// the stage), scaled by the lattice weight wa.
+// weights is added at wall nodes only, through K - 1); half storage
+// interpolates the stored g and adds wa times dI, the interpolated node
+// densities of the direction's stencil (dens_interp).
 template <int A, int NS, typename S, int TY, int SLOTS>
 __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int tx, int ty, const MaskedW& mx,
-                                         const MaskedW& my, float ref, float wa)
+                                         const MaskedW& my, float dI, float wa)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
@@ -211,26 +242,14 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
                  (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
     const int cx = tx + ((cls & 1) ? G::XP : 0);
     const int cy = ty + ((cls & 2) ? 1 : 0);
-    auto ld = [&](int yy, int xx) -> float {
-        if constexpr (G::LOCAL) {
-            // the density tile has the x and y halo; shift into its frame
-            constexpr int W7 = G::bw(3), DX = (cls & 1) ? 0 : G::XP, DY = (cls & 2) ? 0 : 1;
-            const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
-            return fmaf(wa, (float)r[(yy + DY) * W7 + xx + DX], (float)s[yy * W + xx]);
-        } else {
-            return (float)s[yy * W + xx];
-        }
-    };
-    // float storage computes on deviations, half storage decoded each value:
-    // neither adds a reference here (ref is unused)
+    auto ld = [&](int yy, int xx) -> float { return (float)s[yy * W + xx]; };
+    float v;
     if constexpr (cls == 0) {
-        return ld(cy, cx);
+        v = ld(cy, cx);
     } else if constexpr (cls == 1) {
-        const float v = mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1);
-        return v;
+        v = mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1);
     } else if constexpr (cls == 2) {
-        const float v = my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx);
-        return v;
+        v = my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx);
     } else {
         float acc = 0.0f;
 #pragma unroll
@@ -239,13 +258,16 @@ __device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int 
                               mx.w[xi][2] * ld(cy + oy, cx + 1);
             acc += my.w[yi][oy + 1] * row;
         }
-        return acc;
+        v = acc;
     }
+    if constexpr (G::LOCAL) return fmaf(wa, dI, v);
+    else return v;
 }
 
-// Unit lattice speed off the walls: weights (1, 0, 0), the upstream node.
+// Unit lattice speed off the walls: weights (1, 0, 0), the upstream node
+// (half storage: dI is that node's density rho~).
 template <int A, int NS, typename S, int TY, int SLOTS>
-__device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float ref, float wa)
+__device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float dI, float wa)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
@@ -256,13 +278,8 @@ __device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp,
                  (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
     const int cx = tx + ((cls & 1) ? G::XP : 0) - ex;
     const int cy = ty + ((cls & 2) ? 1 : 0) - ey;
-    if constexpr (G::LOCAL) {
-        constexpr int W7 = G::bw(3), DX = (cls & 1) ? 0 : G::XP, DY = (cls & 2) ? 0 : 1;
-        const S* r = reinterpret_cast<const S*>(slot + G::group_offset(7)) + sp * G::plane_elems(7);
-        return fmaf(wa, (float)r[(cy + DY) * W7 + cx + DX], (float)s[cy * W + cx]);
-    } else {
-        return (float)s[cy * W + cx];
-    }
+    if constexpr (G::LOCAL) return fmaf(wa, dI, (float)s[cy * W + cx]);
+    else return (float)s[cy * W + cx];
 }
 
 template <int NS, typename S, int TY, int SLOTS>
@@ -380,34 +397,45 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
         }
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
+        // half storage: this stage's node densities around the node (the
+        // density term of every stencil is taken from them once per stage)
+        float rd[3][3] = {};
+        if constexpr (G::LOCAL)
+            if (ok) dens_block<NS, S, TY, SLOTS>(base, sp, tx, ty, rd);
         if (ok && unit_fast) {
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = 0.0f, wa = p.wl[wclass<1>(A)];
+                const float dI = rd[1 - ev<1>(A, 1)][1 - ev<1>(A, 0)], wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
-                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
+                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
                 } else if constexpr (ez > 0) {
                     // exact shift: node z takes slab z - 1, which arrived two iterations ago
                     f[A] = accA[A];
                     accA[A] = accB[A];
-                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
+                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
                 } else {
-                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, ref, wa);
+                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
                 }
             });
         } else if (ok) {
+            float di[3][3] = {};   // [ey + 1][ex + 1]
+            if constexpr (G::LOCAL)
+                static_for<0, 9>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    di[K / 3][K % 3] = dens_interp<K % 3 - 1, K / 3 - 1>(rd, mx, my);
+                });
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 constexpr int ez = ev<1>(A, 2);
-                const float ref = 0.0f, wa = p.wl[wclass<1>(A)];
+                const float dI = di[ev<1>(A, 1) + 1][ev<1>(A, 0) + 1], wa = p.wl[wclass<1>(A)];
                 if constexpr (ez == 0) {
                     f[A] = accN[A];
-                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref, wa);
+                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, dI, wa);
                 } else {
                     const float R =
-                        solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, ref, wa);
+                        solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, dI, wa);
                     // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
                     f[A] = accA[A] + w[widx(1, ez)] * R;
                     accA[A] = accB[A] + w[widx(0, ez)] * R;
