@@ -71,6 +71,16 @@ __host__ __device__ constexpr int opp(int a)
     return b;
 }
 
+// the first direction whose component d is non-zero (where a sum over that
+// component starts), -1 if none
+template <int LAT>
+__host__ __device__ constexpr int first_dir(int d)
+{
+    for (int a = 0; a < Lat<LAT>::Q; ++a)
+        if (ev<LAT>(a, d) != 0) return a;
+    return -1;
+}
+
 // weight class = number of non-zero components: 0 rest, 1 axis, 2 diagonal
 template <int LAT>
 __host__ __device__ constexpr int wclass(int a)
@@ -472,14 +482,27 @@ __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fo
 template <int LAT, int A, typename T>
 __device__ __forceinline__ T edot(const T (&v)[3])
 {
-    T s = (T)0;
-    if constexpr (ev<LAT>(A, 0) == 1) s += v[0];
-    if constexpr (ev<LAT>(A, 0) == -1) s -= v[0];
-    if constexpr (ev<LAT>(A, 1) == 1) s += v[1];
-    if constexpr (ev<LAT>(A, 1) == -1) s -= v[1];
-    if constexpr (ev<LAT>(A, 2) == 1) s += v[2];
-    if constexpr (ev<LAT>(A, 2) == -1) s -= v[2];
-    return s;
+    // starts from the first non-zero term: without fast-math the compiler has
+    // to keep an explicit 0 + x (it differs from x in the sign of a zero), one
+    // wasted add per call
+    constexpr int e0 = ev<LAT>(A, 0), e1 = ev<LAT>(A, 1), e2 = ev<LAT>(A, 2);
+    if constexpr (e0 != 0) {
+        T s = e0 > 0 ? v[0] : -v[0];
+        if constexpr (e1 == 1) s += v[1];
+        if constexpr (e1 == -1) s -= v[1];
+        if constexpr (e2 == 1) s += v[2];
+        if constexpr (e2 == -1) s -= v[2];
+        return s;
+    } else if constexpr (e1 != 0) {
+        T s = e1 > 0 ? v[1] : -v[1];
+        if constexpr (e2 == 1) s += v[2];
+        if constexpr (e2 == -1) s -= v[2];
+        return s;
+    } else if constexpr (e2 != 0) {
+        return e2 > 0 ? v[2] : -v[2];
+    } else {
+        return (T)0;
+    }
 }
 
 // -------------------------------------------------- moments and relaxation

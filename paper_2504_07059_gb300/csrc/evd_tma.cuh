@@ -473,16 +473,19 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                     f[A] = fmaf(p.wl[wclass<1>(A)], ci, f[A]);
                 });
             }
-            float r = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
-            static_for<0, Q>([&](auto ac) {
+            // sums started from their first term (no explicit 0 + x)
+            float r = f[0], j[3];
+            static_for<1, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
                 r += f[A];
-                if constexpr (ev<1>(A, 0) == 1) j[0] += f[A];
-                if constexpr (ev<1>(A, 0) == -1) j[0] -= f[A];
-                if constexpr (ev<1>(A, 1) == 1) j[1] += f[A];
-                if constexpr (ev<1>(A, 1) == -1) j[1] -= f[A];
-                if constexpr (ev<1>(A, 2) == 1) j[2] += f[A];
-                if constexpr (ev<1>(A, 2) == -1) j[2] -= f[A];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    constexpr int first[3] = {first_dir<1>(0), first_dir<1>(1), first_dir<1>(2)};
+                    const int e = ev<1>(A, d);
+                    if (A == first[d]) j[d] = e > 0 ? f[A] : -f[A];
+                    else if (e == 1) j[d] += f[A];
+                    else if (e == -1) j[d] -= f[A];
+                }
             });
             drho = r;
             if constexpr (Codec<S>::DARITH) r = p.rref[sp] + r;
@@ -588,28 +591,52 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             rr = Codec<S>::rt(rho);
             if (active) Codec<S>::st(fout + (ref_plane<1, NS>(sp) * pstride + node), rr);
         }
-        static_for<0, Q>([&](auto ac) {
-            constexpr int A = decltype(ac)::value;
-            constexpr int C = wclass<1>(A);
-            const float eu = edot<1, A>(u);
-            const float eg = edot<1, A>(p.g);
-            const float ea = edot<1, A>(av);
-            const float t1 = c_inv_cs2 * eu;
-            const float S_ = p.wl[C] * sr * fmaf(csp * eg, 1.0f + t1, -ug);
-            float fs;
-            if constexpr (DA) {   // g* directly: every term small
-                const float phi = fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
-                const float b = fmaf(c_inv_cs2, ea, Bm);
-                // g* = g + (w rho - ref - g)/tau + w rho (phi B + b) + S: one large addition
-                fs = f[A] + fmaf(tau_inv, dt[C] - f[A], fmaf(wr[C], fmaf(phi, tau_inv + b, b), S_));
-            } else {
-                const float feq = wr[C] * fmaf(t1, fmaf(0.5f, t1, 1.0f), U2);
-                const float B = fmaf(c_inv_cs2, ea, Bc);
-                fs = fmaf(omt, f[A], fmaf(feq, B, S_));
-            }
+        // Directions in opposite pairs (A, -A): with t1 = c e.u / c_s^2 and e.a,
+        // e.g odd in e, each update is f + (even part) +- (odd part), the parts
+        // formed once per pair.  Float (deviations):
+        //   g* = g + (w rho - ref - g)/tau + w rho X + S,  X = phi (1/tau + b) + b,
+        //   phi = t1 + t1^2/2 + U2, b = c/cs2 e.a + Bm, S = K (c e.g (1 + t1) - u.g);
+        // half: f* = omt f + w rho (phi B) + S, B = c/cs2 e.a + Bc.
+        const float cg[3] = {csp * p.g[0], csp * p.g[1], csp * p.g[2]};
+        const float tB = DA ? tau_inv + Bm : Bc;
+        auto emit_store = [&](int A, int C, float fs) {
             if (active) {
                 if constexpr (G::LOCAL) Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - p.wl[C] * rr);
                 else Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs);
+            }
+        };
+        static_for<0, Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            constexpr int AB = opp<1>(A);
+            constexpr int C = wclass<1>(A);
+            const float K = p.wl[C] * sr;
+            if constexpr (A == 0) {
+                // rest: t1 = e.a = e.g = 0
+                const float S0 = -K * ug;
+                float fs;
+                if constexpr (DA) fs = f[0] + fmaf(tau_inv, dt[0] - f[0], fmaf(wr[0], fmaf(U2, tB, Bm), S0));
+                else fs = fmaf(omt, f[0], fmaf(wr[0] * U2, Bc, S0));
+                emit_store(0, 0, fs);
+            } else if constexpr (A < AB) {
+                const float t1 = c_inv_cs2 * edot<1, A>(u);
+                const float bO = c_inv_cs2 * edot<1, A>(av);
+                const float ceg = edot<1, A>(cg);
+                const float phiE = fmaf(0.5f * t1, t1, U2);
+                // even and odd parts of X (float) or of phi B (half)
+                const float XE = DA ? fmaf(phiE, tB, fmaf(t1, bO, Bm)) : fmaf(phiE, tB, t1 * bO);
+                const float XO = DA ? fmaf(t1, tB, fmaf(phiE, bO, bO)) : fmaf(t1, tB, phiE * bO);
+                const float E = fmaf(wr[C], XE, K * fmaf(ceg, t1, -ug));
+                const float O = fmaf(wr[C], XO, K * ceg);
+                float fa, fb;
+                if constexpr (DA) {   // g* directly: one large addition per direction
+                    fa = f[A] + fmaf(tau_inv, dt[C] - f[A], E + O);
+                    fb = f[AB] + fmaf(tau_inv, dt[C] - f[AB], E - O);
+                } else {
+                    fa = fmaf(omt, f[A], E + O);
+                    fb = fmaf(omt, f[AB], E - O);
+                }
+                emit_store(A, C, fa);
+                emit_store(AB, C, fb);
             }
         });
     }
