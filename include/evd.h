@@ -235,10 +235,10 @@ evd_status evd_set_force_field(evd_ctx* ctx, const double* k_host);
  * Maxwell-Stefan diffusivities (dL_dD host [ns][ns], symmetric, zero
  * diagonal; NULL to skip) and the body force (dL_dg host [3], z entry 0;
  * NULL to skip).  The reverse sweep applies the transpose of each step:
- * the node-local collision's Jacobian (exact, from forward-mode dual numbers
- * through the collision of Eq. LBE_forcing with tau_ij of Eq.
- * relation_tauij_diff_coeff) and the transposed gather (Eq.
- * Second_order_spatial_interpolation and App. A).  States are recomputed from
+ * the transposed Jacobian of the node-local collision of Eq. LBE_forcing
+ * with tau_ij of Eq. relation_tauij_diff_coeff (exact; by hand-written
+ * reverse mode or by dual numbers, as evd_set_adjoint_mode selects) and the
+ * transposed gather (Eq. Second_order_spatial_interpolation and App. A).  States are recomputed from
  * checkpoints stored every checkpoint_every steps (0: about sqrt(nsteps));
  * memory: (nsteps / checkpoint_every + checkpoint_every + 3) population
  * buffers.  Leaves the context at t = nsteps of this run.  Synchronises. */

@@ -5,21 +5,23 @@
 // collision, theta = (D_ij for i < j, g_x, g_y).  Reverse sweep:
 //   lambda_t  = C_t^T lambda*_t,   dL/dtheta += (dC_t/dtheta)^T lambda*_t,
 //   lambda*_{t-1} = G^T lambda_t.
-// C_t^T is taken exactly from the Jacobian of the collision, obtained by
-// running the collision templates in forward-mode dual numbers; G^T is
-// written out by hand (the scatter of the gather's weights, including the
-// lumped wall terms).
+// C_t^T is exact; G^T is written out by hand (the scatter of the gather's
+// weights, including the lumped wall terms).
 //
 // The collision of Eq. (LBE_forcing) is f*_ia = omt_i f_ia + h_ia(m, theta):
 // apart from the linear term omt_i f_ia (omt_i = 1 - 1/tau_i), it depends on
 // the populations only through the node moments m = (rho_i, J_x,i, J_y,i),
 // rho_i = sum_a f_ia and J_i = sum_a e_a f_ia (Eq. zeroth_order_moment,
 // first_order_moment_force), a constant linear map m = P f.  Hence
-//   C^T lambda* = omt . lambda* + P^T mu,   mu_m = lambda* . dh/dm_m,
-// and dh/dm_m = C s_m - omt . s_m for any population seed s_m with P s_m =
-// the unit vector of m.  So the dual numbers carry 3 NS moment tangents
-// (seeds on the rest and the axis populations) plus the parameters, not one
-// tangent per population.
+//   C^T lambda* = omt . lambda* + P^T mu,   mu_m = lambda* . dh/dm_m.
+// Two kernels form mu and the parameter partials:
+//   k_adj_collide_rev (default): reverse mode written out by hand through the
+//     collision, recomputed in double;
+//   k_adj_collide (cross-check): the step's own collision templates in
+//     forward-mode dual numbers, dh/dm_m = C s_m - omt . s_m for population
+//     seeds s_m with P s_m = the unit vector of m, so the dual numbers carry
+//     3 NS moment tangents (seeds on the rest and the axis populations) plus
+//     the parameters, not one tangent per population.
 #include <cuda_runtime.h>
 
 #include "evd_device.cuh"
