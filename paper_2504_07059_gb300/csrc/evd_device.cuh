@@ -675,7 +675,9 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
         }
         sr[i] = s.rho[i] * p.inv_cs2[i] * p.sfac[i];
     }
-    static_for<0, Q>([&](auto ac) {
+    // the rest direction (and any direction that is its own opposite), as
+    // written in the update above
+    auto single = [&](auto ac) {
         constexpr int A = decltype(ac)::value;
         constexpr int C = wclass<LAT>(A);
         const T eu = edot<LAT, A>(s.u);
@@ -704,6 +706,53 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
                 const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);
                 f[i][A] = fma(p.omt[i], f[i][A], fma(feq, B, S));
+            }
+        }
+    };
+    // Other directions in opposite pairs (A, -A): t1 = c e.u/c_s^2, e.a and
+    // e.g change sign with e (the corrective terms do not), so each update is
+    // f + (even part) +- (odd part), the parts formed once per pair:
+    //   phi B = (phi_E + t1)(B_E + b_O),  phi_E = t1^2/2 + U2, b_O = c/cs2 e.a,
+    //   S = K (c e.g t1 - u.g) + K c e.g,  K = w sr.
+    static_for<0, Q>([&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        constexpr int AB = opp<LAT>(A);
+        if constexpr (A == AB) {
+            single(ac);
+        } else if constexpr (A < AB) {
+            constexpr int C = wclass<LAT>(A);
+            const T eu = edot<LAT, A>(s.u);
+            const T eg = edot<LAT, A>(g);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const T t1 = p.c_inv_cs2[i] * eu;
+                const T bO = p.c_inv_cs2[i] * edot<LAT, A>(av[i]);
+                const T ceg = p.c[i] * eg;
+                const T phiE = fma((T)0.5 * t1, t1, U2[i]);
+                const T K = p.wl[C] * sr[i];
+                T SE = K * fma(ceg, t1, -ug);
+                const T SO = K * ceg;
+                if constexpr (CORR) {
+                    const T eX = edot<LAT, A>(Xc[i]), eY = edot<LAT, A>(Yc[i]);
+                    const T uX = s.u[0] * Xc[i][0] + s.u[1] * Xc[i][1] + s.u[2] * Xc[i][2];
+                    const T qY = s.ueq[i][0] * Yc[i][0] + s.ueq[i][1] * Yc[i][1] + s.ueq[i][2] * Yc[i][2];
+                    const T eq = edot<LAT, A>(s.ueq[i]);
+                    const T c2 = p.c[i] * p.c[i];
+                    const T corr = p.inv_cs2[i] * (p.inv_cs2[i] * c2 * eu * eX - uX) + (p.inv_cs2[i] * c2 * eq * eY - qY);
+                    SE += p.wl[C] * p.sfac[i] * corr;
+                }
+                if constexpr (DA) {   // X = phi (1/tau + b) + b, b = b_O + Bm
+                    const T tB = p.tau_inv[i] + Bm[i];
+                    const T E = fma(wr[i][C], fma(phiE, tB, fma(t1, bO, Bm[i])), SE);
+                    const T O = fma(wr[i][C], fma(t1, tB, fma(phiE, bO, bO)), SO);
+                    f[i][A] += fma(p.tau_inv[i], dt[i][C] - f[i][A], E + O);
+                    f[i][AB] += fma(p.tau_inv[i], dt[i][C] - f[i][AB], E - O);
+                } else {              // B = b_O + Bc
+                    const T E = fma(wr[i][C], fma(phiE, Bc[i], t1 * bO), SE);
+                    const T O = fma(wr[i][C], fma(t1, Bc[i], phiE * bO), SO);
+                    f[i][A] = fma(p.omt[i], f[i][A], E + O);
+                    f[i][AB] = fma(p.omt[i], f[i][AB], E - O);
+                }
             }
         }
     });
