@@ -13,6 +13,7 @@ Array layouts (all float64, C order):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -26,6 +27,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
+_variants = 0
 
 MAXS = 6
 MAXQ = 19
@@ -81,45 +83,89 @@ class Diag(ctypes.Structure):
     ]
 
 
+def _bind(path: str):
+    """Load an oracle library and declare its entry points."""
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    L.or_create.restype = ctypes.c_void_p
+    L.or_create.argtypes = [P(Config)]
+    L.or_destroy.argtypes = [ctypes.c_void_p]
+    L.or_init.restype = ctypes.c_int
+    L.or_init.argtypes = [ctypes.c_void_p, dp, dp]
+    L.or_set_force_field.restype = ctypes.c_int
+    L.or_set_force_field.argtypes = [ctypes.c_void_p, dp]
+    L.or_step.restype = ctypes.c_long
+    L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    L.or_stream_only.argtypes = [ctypes.c_void_p]
+    L.or_collide_only.restype = ctypes.c_int
+    L.or_collide_only.argtypes = [ctypes.c_void_p]
+    L.or_set_f.argtypes = [ctypes.c_void_p, dp]
+    L.or_get_f.argtypes = [ctypes.c_void_p, dp]
+    L.or_time.restype = ctypes.c_long
+    L.or_time.argtypes = [ctypes.c_void_p]
+    L.or_observables.restype = ctypes.c_int
+    L.or_observables.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
+    L.or_mass.argtypes = [ctypes.c_void_p, dp]
+    L.or_collide_node.restype = ctypes.c_int
+    L.or_collide_node.argtypes = [ctypes.c_void_p, dp, dp, P(Diag)]
+    L.or_diag_size.restype = ctypes.c_int
+    L.or_tau_cross.restype = ctypes.c_int
+    L.or_tau_cross.argtypes = [P(Config), dp, dp]
+    L.or_tau_cross_dense.restype = ctypes.c_int
+    L.or_tau_cross_dense.argtypes = [P(Config), dp, dp]
+    L.or_lattice_info.restype = ctypes.c_int
+    L.or_lattice_info.argtypes = [ctypes.c_int, P(ctypes.c_int), dp, P(ctypes.c_int)]
+    L.or_species_info.argtypes = [ctypes.c_void_p, dp, dp, dp]
+    assert L.or_diag_size() == ctypes.sizeof(Diag), "oracle diag layout mismatch"
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            P = ctypes.POINTER
-            dp = P(ctypes.c_double)
-            L.or_create.restype = ctypes.c_void_p
-            L.or_create.argtypes = [P(Config)]
-            L.or_destroy.argtypes = [ctypes.c_void_p]
-            L.or_init.restype = ctypes.c_int
-            L.or_init.argtypes = [ctypes.c_void_p, dp, dp]
-            L.or_set_force_field.restype = ctypes.c_int
-            L.or_set_force_field.argtypes = [ctypes.c_void_p, dp]
-            L.or_step.restype = ctypes.c_long
-            L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
-            L.or_stream_only.argtypes = [ctypes.c_void_p]
-            L.or_collide_only.restype = ctypes.c_int
-            L.or_collide_only.argtypes = [ctypes.c_void_p]
-            L.or_set_f.argtypes = [ctypes.c_void_p, dp]
-            L.or_get_f.argtypes = [ctypes.c_void_p, dp]
-            L.or_time.restype = ctypes.c_long
-            L.or_time.argtypes = [ctypes.c_void_p]
-            L.or_observables.restype = ctypes.c_int
-            L.or_observables.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
-            L.or_mass.argtypes = [ctypes.c_void_p, dp]
-            L.or_collide_node.restype = ctypes.c_int
-            L.or_collide_node.argtypes = [ctypes.c_void_p, dp, dp, P(Diag)]
-            L.or_diag_size.restype = ctypes.c_int
-            L.or_tau_cross.restype = ctypes.c_int
-            L.or_tau_cross.argtypes = [P(Config), dp, dp]
-            L.or_tau_cross_dense.restype = ctypes.c_int
-            L.or_tau_cross_dense.argtypes = [P(Config), dp, dp]
-            L.or_lattice_info.restype = ctypes.c_int
-            L.or_lattice_info.argtypes = [ctypes.c_int, P(ctypes.c_int), dp, P(ctypes.c_int)]
-            L.or_species_info.argtypes = [ctypes.c_void_p, dp, dp, dp]
-            assert L.or_diag_size() == ctypes.sizeof(Diag), "oracle diag layout mismatch"
-            _lib = L
+            _lib = _bind(build())
     return _lib
+
+
+def compile_variant(source: str, tag: str) -> str:
+    """Compile C source text (a modified copy of the oracle, for the tests that
+    check that the pins catch planted mistakes) with the oracle's flags;
+    returns the library path."""
+    global _variants
+    os.makedirs(_BUILD, exist_ok=True)
+    _variants += 1
+    # a fresh file name each time: the dynamic loader keeps a library it has
+    # already loaded under the same path
+    base = os.path.join(_BUILD, f"variant_{tag}_{os.getpid()}_{_variants}")
+    src, so = base + ".c", base + ".so"
+    with open(src, "w") as fh:
+        fh.write(source)
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", so, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return so
+
+
+@contextlib.contextmanager
+def swapped_library(path: str):
+    """Every oracle call inside the block goes to the library at path."""
+    global _lib
+    L = _bind(path)
+    with _lock:
+        old = _lib
+        _lib = L
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = old
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
 
 
 def _dp(a: np.ndarray | None):

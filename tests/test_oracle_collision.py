@@ -5,6 +5,7 @@ Each identity constrains a different term, so a dropped term, a flipped sign or
 a swapped species index in the oracle fails at least one of them:
   * Sum f^(0) = rho_i, Sum e f^(0) = rho_i u_i^eq  (Eq. feqi0 built to this end)
   * Sum S = 0, Sum e S = F_i                       (Eq. CE_EQ52, CE_EQ54)
+  * Sum e e S = u F + F u                          (the second-order part of S)
   * Sum Omega^ij = 0, Sum e Omega^ij = -rho_i rho_j/(rho tau_ij)(u_i^eq - u_j^eq)
     (from Eq. Cross_collision_Sirovich and the equilibrium moments), whose sum
     over j is -Theta_i (Eq. CE_theta_definition), and Sum_i Theta_i = 0
@@ -74,9 +75,16 @@ def test_node_identities(lattice, M, g):
             Dm = 2 if lattice == 0 else 3
             P = np.einsum("a,ak,al->kl", d["feq"][i], ei, ei)[:Dm, :Dm]
             assert np.allclose(P, rho[i] * (cs2[i] * np.eye(Dm) + np.outer(u, u)[:Dm, :Dm]), atol=1e-13)
-            # forcing term
+            # forcing term: zeroth, first and second moments (the last, u F + F u,
+            # from the lattice's fourth-order isotropy; it is the only one of the
+            # three that the second-order part of Eq. CE_forcing_term_discretized
+            # contributes to)
             assert abs(d["S"][i].sum()) < 1e-15
             assert np.allclose(ei.T @ d["S"][i], F_i, atol=1e-16)
+            PS = np.einsum("a,ak,al->kl", d["S"][i], ei, ei)[:Dm, :Dm]
+            uF = (np.outer(u, F_i) + np.outer(F_i, u))[:Dm, :Dm]
+            if np.abs(F_i).max() > 0:
+                assert np.allclose(PS, uF, rtol=1e-10, atol=1e-12 * np.abs(uF).max())
             # self collision: mass zero, momentum F/(2 tau)
             assert abs(d["om_self"][i].sum()) < 1e-14
             assert np.allclose(ei.T @ d["om_self"][i], F_i / (2 * tau[i]), atol=1e-15)
