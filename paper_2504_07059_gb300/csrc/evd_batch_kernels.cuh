@@ -32,16 +32,6 @@ __device__ __forceinline__ void block_sum(const double (&v)[NS], double* __restr
     __syncthreads();
 }
 
-// Asynchronous copy of BYTES (4 or 8) from global to shared memory: the
-// copies of a whole tile are in flight at once without holding registers.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_to_shared(unsigned dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // The member's constants into shared memory (all threads; the caller
 // synchronises before the first use).
 template <typename T>
@@ -129,20 +119,9 @@ k_step_batch(const BatchItem* __restrict__ items, int n_items, const Params<T>* 
                     const int span = (rv1 - rv0 + 1) * nx;
                     const S* src = fin + off + (long long)rv0 * nx;
                     S* dst = tile + (rv0 - r0) * nx;
-                    if constexpr (sizeof(S) >= 4) {
-                        const unsigned d0 = (unsigned)__cvta_generic_to_shared(dst);
-                        for (int q = 0; q < np; ++q)
-                            for (int k = threadIdx.x; k < span; k += BLOCK)
-                                cp_async_to_shared<sizeof(S)>(d0 + (unsigned)((q * tplane + k) * (int)sizeof(S)),
-                                                              src + q * sp.pstride + k);
-                    } else {   // 2-byte elements: plain copies, several in flight
-                        for (int q = 0; q < np; ++q) {
-#pragma unroll 4
-                            for (int k = threadIdx.x; k < span; k += BLOCK) dst[q * tplane + k] = src[q * sp.pstride + k];
-                        }
-                    }
+                    for (int q = 0; q < np; ++q)
+                        for (int k = threadIdx.x; k < span; k += BLOCK) dst[q * tplane + k] = src[q * sp.pstride + k];
                     load_params(spt, params + w.member);
-                    if constexpr (sizeof(S) >= 4) cp_async_wait();
                 }
             }
         }
