@@ -66,7 +66,6 @@ struct evd_batch {
     unsigned* err_flag;
     int mc_every, corr_pending, corr_applied;
     int item_sites, ctas_per_sm, grid;
-    int tile_cap;       // elements of the step's shared-memory tile for this schedule
     int graph_steps;
     std::vector<GraphEntry> graphs;
     long long launches;
@@ -162,7 +161,7 @@ namespace {
 
 BatchArgs args_of(const evd_batch* b)
 {
-    return BatchArgs{b->items_d, b->n_items, b->params_d, b->info_d, b->grid, b->tile_cap};
+    return BatchArgs{b->items_d, b->n_items, b->params_d, b->info_d, b->grid};
 }
 
 cudaError_t dispatch_step(const evd_batch* b, cudaStream_t st, const void* fin, void* fout, int flags,
@@ -266,24 +265,6 @@ evd_status set_schedule(evd_batch* b, int item_sites, int ctas_per_sm)
     b->ctas_per_sm = ctas_per_sm;
     const long long persistent = (long long)ctas_per_sm * b->sm_count;
     b->grid = (ctas_per_sm == 0 || persistent >= b->n_items) ? b->n_items : (int)persistent;
-    // D2Q9 members walled in y: the step stages each item's rows and the rows
-    // on either side in shared memory (every plane); the tile is the largest
-    // such block among the items that fit the budget (the others read global
-    // memory directly)
-    long long tile = 0;
-    if (b->lattice == EVD_D2Q9)
-        for (int m = 0; m < b->n; ++m) {
-            const HostParams& h = b->hp[m];
-            if (!h.wall[1]) continue;
-            const long long planes = (long long)h.ns * b->Q + (b->precision == EVD_FP16_STORE ? h.ns : 0);
-            for (long long node0 = 0; node0 < h.nsites; node0 += item_sites) {
-                const long long cnt = std::min<long long>(item_sites, h.nsites - node0);
-                const long long rows = (node0 + cnt - 1) / h.nx - node0 / h.nx + 3;
-                const long long elems = planes * rows * h.nx;
-                if (elems * (long long)b->elem <= evd::BATCH_TILE_BYTES_MAX) tile = std::max(tile, elems);
-            }
-        }
-    b->tile_cap = (int)tile;
     destroy_graphs(b);
     return EVD_OK;
 }

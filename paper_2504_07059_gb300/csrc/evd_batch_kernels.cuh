@@ -44,16 +44,12 @@ __device__ __forceinline__ void load_params(Params<T>& dst, const Params<T>* __r
 }
 
 // One time step of one work item: sites [node0, node0 + count) of a member
-// whose populations start at fout (written) and at gsrc (read by the gather:
-// the member's input populations, or with SH a shared-memory tile of them
-// laid out by pg, where site node sits at node - gshift).  Not inlined: it
-// runs once per item, and three inlined species counts per kernel make D3Q19
-// compile very slowly.
-template <int LAT, int NS, bool SH, typename S, typename T>
-__device__ __noinline__ void item_step(const Params<T>& p, const Params<T>& pg, const S* __restrict__ gsrc,
-                                          int gshift, S* __restrict__ fout, int node0, int count,
-                                          double* __restrict__ part, unsigned& err, int flags,
-                                          const double* __restrict__ corr)
+// whose populations start at fin / fout.  Not inlined: it runs once per item,
+// and three inlined species counts per kernel make D3Q19 compile very slowly.
+template <int LAT, int NS, typename S, typename T>
+__device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__ fin, S* __restrict__ fout,
+                                          int node0, int count, double* __restrict__ part, unsigned& err,
+                                          int flags, const double* __restrict__ corr)
 {
     constexpr int Q = Lat<LAT>::Q;
     double m[NS];
@@ -65,7 +61,7 @@ __device__ __noinline__ void item_step(const Params<T>& p, const Params<T>& pg, 
         node_force(p, node, gn);
         NodeState<NS, T> s;
         const Nbr nb = neighbours(p, node);
-        gather_all<LAT, NS, S, T, SH>(pg, gsrc, node - gshift, nb, f);
+        gather_all<LAT, NS>(p, fin, node, nb, f);
         if (corr) add_correction<LAT, NS>(p, corr, f);
         moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
         collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
@@ -80,76 +76,27 @@ __device__ __noinline__ void item_step(const Params<T>& p, const Params<T>& pg, 
 // when the grid is smaller than the item count).  The step waits on global
 // loads of the stencil, so residency matters more than registers: six CTAs
 // per SM (at most 85 registers) measured fastest on the D2Q9 tube sweep.
-// D2Q9 members walled in y first copy the item's rows, and one row on either
-// side, of every plane into shared memory (coalesced, all loads in flight at
-// once), and the gather reads that tile; tile_cap is its size in elements
-// (0: no tile), and an item whose block does not fit reads global memory.
 template <int LAT, typename S, typename T>
 __global__ void __launch_bounds__(BLOCK, 6)
 k_step_batch(const BatchItem* __restrict__ items, int n_items, const Params<T>* __restrict__ params,
              const MemberInfo* __restrict__ info, const S* __restrict__ fin, S* __restrict__ fout,
              double* __restrict__ part, unsigned* __restrict__ err_flag, int flags,
-             const double* __restrict__ corr, int tile_cap)
+             const double* __restrict__ corr)
 {
     __shared__ Params<T> sp;
-    __shared__ Params<T> spt;   // sp with the tile's plane stride
-    extern __shared__ __align__(16) unsigned char batch_tile_raw[];
-    S* tile = reinterpret_cast<S*>(batch_tile_raw);
     unsigned err = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const BatchItem w = items[it];
         const long long off = info[w.member].foff;
-        __syncthreads();   // the previous item is done with sp, spt and the tile
+        __syncthreads();   // the previous item is done with sp
         load_params(sp, params + w.member);
-        __syncthreads();
-        // rows r0 .. r1 of the member hold the item and its stencil (walls in
-        // y: rows -1 and ny, when in range of r0 .. r1, are never read)
-        bool staged = false;
-        int r0 = 0, tplane = 0;
-        if constexpr (LAT == 0) {
-            if (tile_cap > 0 && sp.wall[1]) {
-                const int nx = sp.nx;
-                r0 = w.node0 / nx - 1;
-                const int r1 = (w.node0 + w.count - 1) / nx + 1;
-                tplane = (r1 - r0 + 1) * nx;
-                const int np = w.ns * Lat<LAT>::Q + (Codec<S>::LOCAL ? w.ns : 0);
-                staged = (long long)np * tplane <= (long long)tile_cap;
-                if (staged) {
-                    const int rv0 = max(r0, 0), rv1 = min(r1, sp.ny - 1);
-                    const int span = (rv1 - rv0 + 1) * nx;
-                    const S* src = fin + off + (long long)rv0 * nx;
-                    S* dst = tile + (rv0 - r0) * nx;
-                    for (int q = 0; q < np; ++q)
-                        for (int k = threadIdx.x; k < span; k += BLOCK) dst[q * tplane + k] = src[q * sp.pstride + k];
-                    load_params(spt, params + w.member);
-                }
-            }
-        }
-        __syncthreads();
-        if (staged && threadIdx.x == 0) spt.pstride = tplane;
         __syncthreads();
         const double* c = corr ? corr + (long long)w.member * MAXS : nullptr;
         double* pt = part + (long long)it * MAXS;
-        const S* g = fin + off;
-        S* o = fout + off;
-        const int sh = r0 * sp.nx;
-        bool done = false;
-        if constexpr (LAT == 0) {
-            if (staged) {
-                switch (w.ns) {
-                    case 1: item_step<LAT, 1, true>(sp, spt, tile, sh, o, w.node0, w.count, pt, err, flags, c); break;
-                    case 2: item_step<LAT, 2, true>(sp, spt, tile, sh, o, w.node0, w.count, pt, err, flags, c); break;
-                    default: item_step<LAT, 3, true>(sp, spt, tile, sh, o, w.node0, w.count, pt, err, flags, c); break;
-                }
-                done = true;
-            }
-        }
-        if (!done) {
-            switch (w.ns) {
-                case 1: item_step<LAT, 1, false>(sp, sp, g, 0, o, w.node0, w.count, pt, err, flags, c); break;
-                case 2: item_step<LAT, 2, false>(sp, sp, g, 0, o, w.node0, w.count, pt, err, flags, c); break;
-                default: item_step<LAT, 3, false>(sp, sp, g, 0, o, w.node0, w.count, pt, err, flags, c); break;
-            }
+        switch (w.ns) {
+            case 1: item_step<LAT, 1>(sp, fin + off, fout + off, w.node0, w.count, pt, err, flags, c); break;
+            case 2: item_step<LAT, 2>(sp, fin + off, fout + off, w.node0, w.count, pt, err, flags, c); break;
+            default: item_step<LAT, 3>(sp, fin + off, fout + off, w.node0, w.count, pt, err, flags, c); break;
         }
     }
     if (err) atomicOr(err_flag, err);
@@ -303,10 +250,8 @@ cudaError_t batch_step(const BatchArgs& a, const void* fin, void* fout, double* 
                        const double* corr, cudaStream_t st)
 {
     if (a.n_items == 0) return cudaSuccess;
-    const int tile_cap = LAT == 0 ? a.tile_cap : 0;
-    k_step_batch<LAT, S, T><<<a.grid, BLOCK, (size_t)tile_cap * sizeof(S), st>>>(
-        a.items, a.n_items, (const Params<T>*)a.params, a.info, (const S*)fin, (S*)fout, part, err, flags, corr,
-        tile_cap);
+    k_step_batch<LAT, S, T><<<a.grid, BLOCK, 0, st>>>(a.items, a.n_items, (const Params<T>*)a.params, a.info,
+                                                      (const S*)fin, (S*)fout, part, err, flags, corr);
     return cudaGetLastError();
 }
 

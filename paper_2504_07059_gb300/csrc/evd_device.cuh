@@ -202,7 +202,6 @@ template <> struct Codec<double> {
     static constexpr bool LOCAL = false;
     static constexpr bool DARITH = false;
     static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
-    static __device__ __forceinline__ double ls(const double* p) { return *p; }   // any state space
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <> struct Codec<float> {
@@ -214,7 +213,6 @@ template <> struct Codec<float> {
     // momenta and forcing terms of near-rest mixtures
     static constexpr bool DARITH = true;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ float ls(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <> struct Codec<__half> {
@@ -222,7 +220,6 @@ template <> struct Codec<__half> {
     static constexpr bool LOCAL = true;
     static constexpr bool DARITH = false;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ float ls(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
     // the value a float takes once stored
     static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
@@ -268,9 +265,7 @@ __host__ __device__ constexpr int widx(int o, int e) { return o == -e ? 0 : (o =
 // Interior node: f_a(O) = sum over the 1/3/9 stencil nodes O + o of
 // W(o) f*_a(O + o), the tensor product of 1-D weights along the (one or two)
 // dimensions direction a moves in.
-// SH: fin points to a shared-memory tile (plain loads instead of the
-// read-only global path), laid out with p.pstride and node as the tile's.
-template <int LAT, int NS, int I, int A, typename S, typename T, bool SH = false>
+template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __restrict__ fin, int node,
                                              const Nbr& nb)
 {
@@ -280,13 +275,9 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
     const T wa = p.wl[wclass<LAT>(A)];
     // the stored value at offset o, decoded with that node's own reference
     // where the storage keeps one per node
-    auto ld = [](const S* q) -> T {
-        if constexpr (SH) return (T)Codec<S>::ls(q);
-        else return (T)Codec<S>::ld(q);
-    };
     auto ldv = [&](long long o) -> T {
-        if constexpr (Codec<S>::LOCAL) return fma(wa, ld(rplane + o), ld(plane + o));
-        else return ld(plane + o);
+        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(plane + o));
+        else return (T)Codec<S>::ld(plane + o);
     };
     T acc;
     if constexpr (ex == 0 && ey == 0 && ez == 0) {
@@ -377,7 +368,7 @@ __device__ __forceinline__ T lumped(const Params<T>& p, int I, const Nbr& nb, bo
 
 // Wall-adjacent node: only fluid stencil nodes contribute, plus the lumped
 // weight of O's own populations in directions a and its opposite.
-template <int LAT, int NS, int I, int A, typename S, typename T, bool SH = false>
+template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict__ fin, int node,
                                          const Nbr& nb)
 {
@@ -392,13 +383,9 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
     const T ref = (T)0;
     T ksum = (T)0;
     // stored value of plane q at offset o, decoded (node reference if kept)
-    auto ld = [](const S* q) -> T {
-        if constexpr (SH) return (T)Codec<S>::ls(q);
-        else return (T)Codec<S>::ld(q);
-    };
     auto ldv = [&](const S* q, long long o) -> T {
-        if constexpr (Codec<S>::LOCAL) return fma(wa, ld(rplane + o), ld(q + o));
-        else return ld(q + o);
+        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(q + o));
+        else return (T)Codec<S>::ld(q + o);
     };
     T acc = (T)0;
 #pragma unroll
@@ -427,7 +414,7 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
     return acc;
 }
 
-template <int LAT, int NS, typename S, typename T, bool SH = false>
+template <int LAT, int NS, typename S, typename T>
 __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restrict__ fin, int node,
                                            const Nbr& nb, T (&f)[NS][Lat<LAT>::Q])
 {
@@ -437,7 +424,7 @@ __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restri
             constexpr int I = decltype(ic)::value;
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_interior<LAT, NS, I, A, S, T, SH>(p, fin, node, nb);
+                f[I][A] = gather_interior<LAT, NS, I, A>(p, fin, node, nb);
             });
         });
     } else {
@@ -445,7 +432,7 @@ __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restri
             constexpr int I = decltype(ic)::value;
             static_for<0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_wall<LAT, NS, I, A, S, T, SH>(p, fin, node, nb);
+                f[I][A] = gather_wall<LAT, NS, I, A>(p, fin, node, nb);
             });
         });
     }

@@ -83,13 +83,7 @@ struct BatchArgs {
     const void* params;      // Params<T>[members] on the device
     const MemberInfo* info;  // [members] on the device
     int grid;                // CTAs of the step launch (persistent when < n_items)
-    int tile_cap;            // elements of the shared-memory tile of the step (0: none)
 };
-
-// Dynamic shared memory the batched step may use to stage a work item's rows
-// (below the 48 KB a launch gets without opting in, with room for the
-// kernel's static shared memory).
-constexpr int BATCH_TILE_BYTES_MAX = 44 * 1024;
 
 template <int PREC, int LAT>
 struct BatchLaunch {
