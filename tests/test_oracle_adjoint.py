@@ -4,7 +4,10 @@ so (1) its populations after N steps and its loss equal the C oracle's to
 rounding; (2) its reverse-mode gradient equals fourth-order finite
 differences of the C oracle's loss (independent code) to the differences'
 own accuracy; (3) reverse mode equals forward mode along random directions
-(the dot-product test <grad L, v> = dL(theta + s v)/ds)."""
+(the dot-product test <grad L, v> = dL(theta + s v)/ds).  Mistakes planted
+in the restatement (the force ignored in the collision, the wall rule
+reversed, one diffusivity cut off from the autograd graph) fail the pin that
+guards them."""
 import numpy as np
 import pytest
 import torch
@@ -102,3 +105,53 @@ def test_reverse_mode_equals_forward_mode():
         v = torch.as_tensor(2.0 * W.uniform01(1440 + s, len(theta)) - 1.0) * scale
         _, dL = torch.func.jvp(loss, (theta,), (v,))
         assert abs(float(dL) - float(grad @ v)) <= 1e-12 * abs(float(dL)), (float(dL), float(grad @ v))
+
+
+class _NoForceInCollision(DA.Model):
+    """Planted mistake: the collision ignores the body force."""
+    def collide(self, f, D, g):
+        zero = [g[0] * 0.0, g[1] * 0.0]
+        return super().collide(f, D, zero)
+
+
+class _WallRuleReversed(DA.Model):
+    """Planted mistake: weight crossing a wall is kept in the opposite
+    direction when it heads away from the wall, and vice versa."""
+    def _plan(self):
+        plan = super()._plan()
+        return [[[(w, dx, dy, free, into, keep) for (w, dx, dy, free, keep, into) in terms]
+                 for terms in per_a] for per_a in plan]
+
+
+class _DiffusivityDetached(DA.Model):
+    """Planted mistake: tau_ij sees D_12 as a constant, so the forward map is
+    exact but the gradient misses every path from D_12 through tau."""
+    def tau_cross(self, rho, D):
+        return super().tau_cross(rho, {k: (v.detach() if k in ((0, 1), (1, 0)) else v) for k, v in D.items()})
+
+
+@pytest.mark.parametrize("mutant,pin", [(_NoForceInCollision, "forward"), (_WallRuleReversed, "forward"),
+                                        (_DiffusivityDetached, "gradient")])
+def test_planted_mistakes_fail_a_pin(monkeypatch, mutant, pin):
+    """Each mistake planted in the tensor restatement fails the pin that
+    guards it: the forward map against the C oracle, or the gradient against
+    finite differences of the C oracle's loss."""
+    shape, walls, M, dp, g, steps, wl, n0, target = setup("ternary-walls-y")
+    m = mutant(shape, walls, M, 1.0)
+    if pin == "forward":
+        _, o = c_oracle_loss(shape, walls, M, wl.x, n0, steps, target, dp, g)
+        f = m.run(wl.x, n0, steps, dp, g).numpy()
+        fc = o.get_f()[:, :, 0]
+        assert np.abs(f - fc).max() > 1e-6 * np.abs(fc).max()
+    else:
+        monkeypatch.setattr(DA, "Model", mutant)
+        L, dd, dg = DA.loss_and_gradient(shape, walls, M, 1.0, wl.x, target, steps, dp, g, n0)
+        L0, _ = c_oracle_loss(shape, walls, M, wl.x, n0, steps, target, dp, g)
+        assert abs(L - L0) <= 1e-13 * L0            # the forward map is untouched
+        k = 0
+        e = np.zeros(len(dp))
+        e[k] = 1e-3 * dp[k]
+        Lc = lambda d: c_oracle_loss(shape, walls, M, wl.x, n0, steps, target, d, g)[0]
+        dp_ = np.asarray(dp)
+        fd = (8 * (Lc(dp_ + e) - Lc(dp_ - e)) - (Lc(dp_ + 2 * e) - Lc(dp_ - 2 * e))) / (12 * e[k])
+        assert abs(dd[k] - fd) > 1e-3 * abs(fd)    # far outside the 1e-8 the pin allows
