@@ -52,9 +52,13 @@ FALLBACK_HBM_GBS = 6800.0
 # A change to those sources changes the digest and the entry no longer applies.
 NCU_TRAFFIC = {
     # 128^3 captures, x8 for a 256^3 launch: FP32 545.6 MB read + 437.8 MB written,
-    # FP16 storage 268.3 MB read + 213.9 MB written
-    ("38d5b5e11651c842", "stratification", 256, "fp32"): 7867.1e6,
-    ("38d5b5e11651c842", "stratification", 256, "fp16"): 3858.1e6,
+    # FP16 storage 268.3 MB read + 213.9 MB written.  Captured from sources with
+    # digest 38d5b5e11651c842; the sources below differ from them only in the
+    # general collision template, which k_step_tma does not instantiate, and
+    # k_step_tma<3, float, 2, 3> and <3, __half, 2, 4> compile to byte-identical
+    # code from both (compared without line information)
+    ("90840397bbc90fa6", "stratification", 256, "fp32"): 7867.1e6,
+    ("90840397bbc90fa6", "stratification", 256, "fp16"): 3858.1e6,
 }
 
 
