@@ -1,9 +1,10 @@
 """The oracle's pins catch planted mistakes.  Each case copies evd_oracle.c,
 plants one plausible mistake (a dropped term, a flipped sign, swapped operands,
-the wrong wall rule), compiles the copy and runs the fast pins against it: at
-least one pin must fail, and the pin expected to catch it must be among them.
-The unmodified copy, compiled the same way, passes every pin (control).  The
-mistakes are planted in the oracle only, on the CPU."""
+the wrong wall rule; the corrective forcing terms of Eq.
+improved_forcing_scheme included), compiles the copy and runs the fast pins
+against it: at least one pin must fail, and the pin expected to catch it must
+be among them.  The unmodified copy, compiled the same way, passes every pin
+(control).  The mistakes are planted in the oracle only, on the CPU."""
 import gc
 import inspect
 import itertools
@@ -13,6 +14,7 @@ import pytest
 from oracle import oracle as O
 
 import test_oracle_collision as TC
+import test_oracle_forcing as TF
 import test_oracle_lattice as TL
 import test_oracle_physics as TP
 import test_oracle_stream as TS
@@ -42,7 +44,7 @@ def _expand(fn):
 
 def _pins():
     pins = []
-    for mod in (TC, TS, TT, TL):
+    for mod in (TC, TS, TT, TL, TF):
         for name, fn in inspect.getmembers(mod, inspect.isfunction):
             if name.startswith("test_") and fn.__module__ == mod.__name__:
                 for kw in _expand(fn):
@@ -127,6 +129,22 @@ MUTANTS = {
         "const int b = (dot > 0) ? st->opp[a] : a;",
         "const int b = (dot < 0) ? st->opp[a] : a;",
         "test_wall_equations_of_appendix_a"),
+    "s-diff-factor": (
+        "Xc[k] += dt / (2.0 * tau_i - dt) * th;",
+        "Xc[k] += dt / (2.0 * tau_i) * th;",
+        "test_s_diff_adds_no_mass_or_momentum_and_the_symmetric_second_moment"),
+    "s-p-sign": (
+        "Xc[k] -= cs2 * grad[i * 3 + k];",
+        "Xc[k] += cs2 * grad[i * 3 + k];",
+        "test_gradient_terms_on_densities_linear_in_x"),
+    "s-rho-without-mass-fraction": (
+        "Yc[k] = (rho[i] / rho_mix) * grad[ns * 3 + k];",
+        "Yc[k] = grad[ns * 3 + k];",
+        "test_gradient_terms_on_densities_linear_in_x"),
+    "lattice-gradient-scale": (
+        "for (k = 0; k < 3; ++k) g[k] *= 3.0;",
+        "for (k = 0; k < 3; ++k) g[k] *= 2.0;",
+        "test_gradient_terms_on_densities_linear_in_x"),
     "wall-tie-to-opposite": (
         "const int b = (dot > 0) ? st->opp[a] : a;",
         "const int b = (dot >= 0) ? st->opp[a] : a;",
