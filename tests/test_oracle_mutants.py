@@ -51,7 +51,8 @@ def _pins():
                     if set(inspect.signature(fn).parameters) == set(kw):
                         pins.append((name, fn, kw))
     # fast whole-step pins (no fixtures)
-    for name in ("test_periodic_box_momentum_grows_by_the_total_force",
+    for name in ("test_initial_state_is_at_rest_and_reads_back_its_fields",
+                 "test_periodic_box_momentum_grows_by_the_total_force",
                  "test_shear_wave_decays_with_the_common_viscosity",
                  "test_force_field_of_zeros_and_uniform_field_reduce_to_plain_gravity"):
         fn = getattr(TP, name)
@@ -145,6 +146,18 @@ MUTANTS = {
         "for (k = 0; k < 3; ++k) g[k] *= 3.0;",
         "for (k = 0; k < 3; ++k) g[k] *= 2.0;",
         "test_gradient_terms_on_densities_linear_in_x"),
+    "initial-velocity-sign": (
+        "ui0[k] = 0.0 - rho_i * a0[k] * dt / (2.0 * rho_i);",
+        "ui0[k] = 0.0 + rho_i * a0[k] * dt / (2.0 * rho_i);",
+        "test_initial_state_is_at_rest_and_reads_back_its_fields"),
+    "readout-mole-fraction-without-molar-mass": (
+        "if (x) x[(long)i * nsites + X] = dg.rho[i] / (dg.n * st->cfg.M[i]);",
+        "if (x) x[(long)i * nsites + X] = dg.rho[i] / dg.n;",
+        "test_initial_state_is_at_rest_and_reads_back_its_fields"),
+    "force-field-ignored": (
+        "a[k] = st->cfg.g[k] + (st->acc ? st->acc[(long)k * st->nsites + X] : 0.0);",
+        "a[k] = st->cfg.g[k];",
+        "test_force_field_of_zeros_and_uniform_field_reduce_to_plain_gravity"),
     "wall-tie-to-opposite": (
         "const int b = (dot > 0) ? st->opp[a] : a;",
         "const int b = (dot >= 0) ? st->opp[a] : a;",

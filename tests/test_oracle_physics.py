@@ -16,6 +16,8 @@
   the cross collision sums to zero over species and streaming conserves.
 * A shear wave decays with the common kinematic viscosity
   nu = (tau_1 - 1/2) c_s1^2 that every species shares (Sec. 3).
+* The initial state is at rest (Sec. 4.1, 4.2) and reads back the fields it
+  was made from.
 """
 import numpy as np
 import pytest
@@ -192,3 +194,28 @@ def test_ultracentrifuge_steady_profile_follows_the_closed_form():
     # and the species mass stays exact up to rounding (T steps x 4 eps)
     m0 = np.array([(wl.x[i] * wl.M[i] * wl.n).sum() for i in range(2)])
     assert np.abs(o.mass() / m0 - 1.0).max() < 18000 * 4 * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("lattice,shape,mask,M,g", [
+    (W.D2Q9, (5, 7), W.WALL_Y, (1.0, 3.0, 7.0), (2e-5, -3e-5)),
+    (W.D3Q19, (3, 4, 5), W.WALL_X | W.WALL_Y | W.WALL_Z, (16.0, 28.0, 44.0), (1e-5, -2e-5, 3e-5))])
+def test_initial_state_is_at_rest_and_reads_back_its_fields(lattice, shape, mask, M, g):
+    """Sec. 4.1 and 4.2 start every species at rest: with the forced
+    u_i^eq = j_i/rho_i + g/2 (Eq. first_order_moment_force) the initial
+    populations carry u_i0 = -g/2, so the read-out species and mixture
+    velocities are zero; rho_i = x_i M_i n, and the readout x_i = rho_i/(n M_i)
+    returns the mole fractions it started from."""
+    wl = W.random_mixture(lattice, shape, mask, M, g=g, stream=1450, n_amp=0.1)
+    o = O.Oracle(lattice, shape, mask, M, wl.D, 1.0, g)
+    o.init(wl.x, wl.n)
+    obs = o.observables()
+    # rounding of the first moments of O(0.1) populations: ~1e-17, against
+    # |g| ~ 3e-5 for a sign slip
+    assert np.abs(obs["u"]).max() < 1e-15
+    assert np.abs(obs["ui"]).max() < 1e-15
+    n = wl.n.reshape(obs["x"].shape[1:])
+    # a handful of roundings (sums of Q populations, n, one division):
+    # observed 6.7e-16
+    for i, Mi in enumerate(M):
+        assert np.allclose(obs["rho"][i], wl.x[i] * Mi * n, rtol=4e-15, atol=0)
+    assert np.allclose(obs["x"], wl.x, rtol=4e-15, atol=0)
