@@ -158,6 +158,18 @@ MUTANTS = {
         "a[k] = st->cfg.g[k] + (st->acc ? st->acc[(long)k * st->nsites + X] : 0.0);",
         "a[k] = st->cfg.g[k];",
         "test_force_field_of_zeros_and_uniform_field_reduce_to_plain_gravity"),
+    "d3q19-weights-swapped": (
+        "w[a] = (a == 0) ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);",
+        "w[a] = (a == 0) ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 36.0 : 1.0 / 18.0);",
+        "test_weights_are_isotropic_with_cs2_one_third"),
+    "z-stencil-dropped": (
+        "for (d[2] = (Dm == 3 ? -1 : 0); d[2] <= (Dm == 3 ? 1 : 0); ++d[2])",
+        "for (d[2] = 0; d[2] <= 0; ++d[2])",
+        "test_streaming_conserves_each_species_mass"),
+    "opposite-table-ignores-z": (
+        "if (e[b][0] == -e[a][0] && e[b][1] == -e[a][1] && e[b][2] == -e[a][2]) opp[a] = b;",
+        "if (e[b][0] == -e[a][0] && e[b][1] == -e[a][1] && e[b][2] == e[a][2]) opp[a] = b;",
+        "test_weights_are_isotropic_with_cs2_one_third"),
     "wall-tie-to-opposite": (
         "const int b = (dot > 0) ? st->opp[a] : a;",
         "const int b = (dot >= 0) ? st->opp[a] : a;",
