@@ -77,6 +77,12 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def traffic_for(digest: str, workload: str, size: int, precision: str):
+    """ncu DRAM bytes of one step launch captured from kernel sources with
+    this digest, or None (sources changed since the capture, or none)."""
+    return NCU_TRAFFIC.get((digest, workload, size, precision))
+
+
 def measured_peaks() -> tuple[float, str]:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -541,7 +547,7 @@ def run_ours(args) -> None:
     bpl = bytes_per_ssu(wl, prec) * ns * nsites
     achieved = bpl / (ms / args.steps * 1e-3) / 1e9
     digest = kernel_digest()
-    traffic = NCU_TRAFFIC.get((digest, args.workload, args.size, prec))
+    traffic = traffic_for(digest, args.workload, args.size, prec)
 
     # end to end through the public API with pinned host buffers: upload the
     # initial mole fractions, run the same number of steps, read the mole

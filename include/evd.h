@@ -264,6 +264,19 @@ evd_status evd_set_adjoint_mode(evd_ctx* ctx, int mode);
  * apply. */
 evd_status evd_set_tile_rows(evd_ctx* ctx, int rows);
 
+/* Poll limit of the TMA-staged step's waits for its tile copies (not in the
+ * paper; the failure-detection path).  Every wait of a step for the
+ * mbarrier that completes a tile copy polls at most `polls` times; a wait
+ * that gives up makes every CTA that saw it stop stepping, wait (with the
+ * default limit) for the copies it still has in flight, and set
+ * EVD_ERR_TIMEOUT, which the next evd_check returns.  The output buffer is
+ * then partly written and the context should be re-initialised (set_fields
+ * or set_populations) or destroyed.  polls < 0 restores the default 2^22
+ * (far longer than any copy takes); 0 makes every wait give up at once, which
+ * is how the timeout path is tested.  Applies to the TMA step only.
+ * EVD_ERR_ARG for a NULL ctx. */
+evd_status evd_set_wait_limit(evd_ctx* ctx, int polls);
+
 /* FP64 species-mass correction (not in the paper; a precision device for
  * FP32/FP16 storage).  Every `every` steps the step kernel also reduces the
  * per-species mass of f_t in double precision; the deficit from the initial
@@ -291,7 +304,9 @@ evd_status evd_get_target_mass(evd_ctx* ctx, double* m_host);
  * file-scope device array of 1024 x 3 doubles (24 KiB), present on every
  * device that loads the library until the process exits.  Its address is
  * looked up on the first call on each device (with that device current),
- * so make that first call before any stream capture.  All calls share the
+ * and again on the first call after that device's context was torn down
+ * and created anew (cudaDeviceReset); make such a first call before any
+ * stream capture.  All calls share the
  * array: calls that overlap on the GPU (different streams, or several host
  * threads) race and give wrong sums; serialise them.  Returns EVD_ERR_ARG
  * for sizes beyond the limits above and EVD_ERR_CUDA if a launch fails;

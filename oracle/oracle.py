@@ -13,10 +13,13 @@ Array layouts (all float64, C order):
 """
 from __future__ import annotations
 
+import atexit
 import contextlib
 import ctypes
 import os
+import shutil
 import subprocess
+import tempfile
 import threading
 
 import numpy as np
@@ -129,16 +132,28 @@ def lib():
     return _lib
 
 
+_variant_dir = None
+
+
+def _variants_dir() -> str:
+    """A private temporary directory for compiled variants, removed when the
+    process exits (a loaded library stays mapped after its file is gone)."""
+    global _variant_dir
+    if _variant_dir is None:
+        _variant_dir = tempfile.mkdtemp(prefix="evd_oracle_variants_")
+        atexit.register(shutil.rmtree, _variant_dir, True)
+    return _variant_dir
+
+
 def compile_variant(source: str, tag: str) -> str:
     """Compile C source text (a modified copy of the oracle, for the tests that
-    check that the pins catch planted mistakes) with the oracle's flags;
-    returns the library path."""
+    check that the pins catch planted mistakes) with the oracle's flags, in a
+    temporary directory removed at exit; returns the library path."""
     global _variants
-    os.makedirs(_BUILD, exist_ok=True)
     _variants += 1
     # a fresh file name each time: the dynamic loader keeps a library it has
     # already loaded under the same path
-    base = os.path.join(_BUILD, f"variant_{tag}_{os.getpid()}_{_variants}")
+    base = os.path.join(_variants_dir(), f"variant_{tag}_{_variants}")
     src, so = base + ".c", base + ".so"
     with open(src, "w") as fh:
         fh.write(source)

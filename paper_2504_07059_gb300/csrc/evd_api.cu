@@ -198,6 +198,7 @@ void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
     h.nsites = g->nx * g->ny * g->nz;
     h.pstride = plane_stride(g);
     h.flags = s->flags;
+    h.wait_polls = kWaitPolls;
     for (int k = 0; k < 3; ++k) {
         h.wall[k] = ((g->wall_mask >> (2 * k)) & 3u) ? 1 : 0;
         h.g[k] = s->g[k];
@@ -972,6 +973,13 @@ evd_status evd_set_tile_rows(evd_ctx* c, int rows)
         return fail(c, EVD_ERR_CUDA, "could not rebuild the tile copies");
     }
     c->tma_blocks = evd::TmaLaunch::grid(c->hp, rows);
+    return EVD_OK;
+}
+
+evd_status evd_set_wait_limit(evd_ctx* c, int polls)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    c->hp.wait_polls = polls < 0 ? evd::kWaitPolls : polls;
     return EVD_OK;
 }
 

@@ -35,7 +35,11 @@ struct HostParams {
     const void* kf;          // device [3][nsites] force field in the arithmetic type, or nullptr
     unsigned flags;          // corrective forcing terms (EVD_FORCE_S_DIFF / _S_P / _S_RHO)
     const void* rhof;        // device [ns + 1][nsites] densities of f_t for the gradient terms
+    int wait_polls;          // polls of a TMA-step wait for a tile copy before it gives up
 };
+
+// Default of HostParams::wait_polls: far longer than any tile copy takes.
+constexpr int kWaitPolls = 1 << 22;
 
 // Host-side checks and constants shared by the single-lattice context and the
 // batch of lattices (evd_api.cu).

@@ -6,7 +6,12 @@
 // live in the file-scope device array below instead of memory obtained from
 // cudaMalloc.  Host code must not pass the array's name to a kernel: on the
 // host that name is only a stand-in, not a device address.  The device
-// address is looked up once per device with cudaGetSymbolAddress and cached.
+// address is looked up with cudaGetSymbolAddress, with the device current,
+// on the first call in each CUDA context of a device, and cached for that
+// context: a context torn down and created again (cudaDeviceReset, a new
+// primary context) loads the module afresh, so the address is looked up again.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -19,11 +24,13 @@ namespace {
 
 constexpr int NA_BLOCK = 256;
 constexpr int NA_MAX_BLOCKS = 1024;                 // grid-stride beyond this
-constexpr int NA_MAX_SPECIES = EVD_MAX_SPECIES;
+constexpr int NA_MAX_SPECIES = 3;                  // the scratch holds partials for 3 species
 constexpr int NA_MAX_DEVICES = 64;
 
 std::mutex g_na_mutex;
-double* g_na_scratch[NA_MAX_DEVICES] = {};          // cached device address per device
+// cached device address per device, valid for the context it was resolved in
+double* g_na_scratch[NA_MAX_DEVICES] = {};
+CUcontext g_na_ctx[NA_MAX_DEVICES] = {};
 
 }  // namespace
 
@@ -75,17 +82,42 @@ evd_k_noalloc_mass_finish(const double* __restrict__ part, int nblocks, int ns, 
 
 namespace {
 
+// The driver's cuCtxGetCurrent, through the runtime's entry-point query (the
+// library links the runtime only).
+cudaError_t current_context(CUcontext* ctx)
+{
+    static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+    if (!get) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        get = (PFN_cuCtxGetCurrent_v4000)fn;
+    }
+    return get(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorContextIsDestroyed;
+}
+
 // Device address of the partials on the current device: resolved with that
-// device current on the first call there, cached afterwards.
+// device current on the first call in its current context, cached for that
+// context afterwards.
 cudaError_t scratch_address(int dev, double** out)
 {
     std::lock_guard<std::mutex> lock(g_na_mutex);
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (!g_na_scratch[dev]) {
+    CUcontext ctx = nullptr;
+    cudaError_t e = current_context(&ctx);
+    if (e != cudaSuccess) return e;
+    if (!ctx || !g_na_scratch[dev] || g_na_ctx[dev] != ctx) {
+        // the lookup also makes the runtime bind the device's primary
+        // context where none is current yet; the context is read after it
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, evd_noalloc_partials);
+        e = cudaGetSymbolAddress(&p, evd_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        e = current_context(&ctx);
         if (e != cudaSuccess) return e;
         g_na_scratch[dev] = (double*)p;
+        g_na_ctx[dev] = ctx;
     }
     *out = g_na_scratch[dev];
     return cudaSuccess;

@@ -128,10 +128,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait: false after 2^22 polls (far longer than any copy takes).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
+// Bounded wait: false after `polls` polls.  The step's waits take
+// WAIT_POLLS (far longer than any copy takes) unless the caller lowers it.
+constexpr int WAIT_POLLS = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, int polls = WAIT_POLLS)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -286,7 +288,8 @@ template <int NS, typename S, int TY, int SLOTS>
 __global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
-           const double* __restrict__ corr, const float4* __restrict__ lumps, int ntx, int nty, int zchunk)
+           const double* __restrict__ corr, const float4* __restrict__ lumps, int ntx, int nty, int zchunk,
+           int wait_polls)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int Q = 19;
@@ -363,6 +366,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     double mass_acc = 0.0;
     unsigned err = 0;
     bool failed = false;
+    int fail_idx = 0;   // iteration whose wait gave up
 
     for (int idx = 0; idx < nstage; ++idx) {
         const int k = kfirst + idx;
@@ -396,7 +400,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             });
             if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
         }
-        const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1));
+        const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1), wait_polls);
         // half storage: this stage's node densities around the node (the
         // density term of every stencil is taken from them once per stage)
         float rd[3][3] = {};
@@ -499,7 +503,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         // one barrier per iteration: the exchange, the release of the stage
         // just read, and agreement on a failed wait
         failed = __syncthreads_or(!ok);
-        if (failed) break;
+        if (failed) { fail_idx = idx; break; }
         if (!emit) continue;
 
         // ---- species coupling (every thread of the node recomputes it)
@@ -642,11 +646,21 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     }
 
     if (failed) {
-        // never expected: report, let copies still in flight land, and leave
+        // never expected: report, let every copy still in flight land in this
+        // CTA's shared memory, and leave.  In flight are the stages issued up
+        // to iteration fail_idx: fail_idx .. fail_idx + SLOTS - 1 (those that
+        // exist); stage s completes phase s / SLOTS of the barrier of slot
+        // s % SLOTS, so each is waited for with that phase's parity (a stage
+        // that already landed returns at once).  These waits always take the
+        // full poll count.
+        cp_async_wait_all();   // this thread's wall-population copies
         if (threadIdx.x == 0) {
             atomicOr(err_flag, ERR_TIMEOUT);
-            for (int q = 0; q < SLOTS; ++q) (void)mbar_wait_bounded(full(q), 0u);
+            const int last = min(fail_idx + SLOTS - 1, nstage - 1);
+            for (int s = fail_idx; s <= last; ++s)
+                (void)mbar_wait_bounded(full(s % SLOTS), (unsigned)((s / SLOTS) & 1), WAIT_POLLS);
         }
+        __syncthreads();
         return;
     }
     if (err) atomicOr(err_flag, err);

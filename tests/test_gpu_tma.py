@@ -87,3 +87,32 @@ def test_tma_kernel_is_rejected_where_it_does_not_apply(evd):
     sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp32")
     assert evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_TMA     # the default where it applies
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_tma_wait_timeout_reports_and_leaves_the_device_usable(evd, precision):
+    """The failure path of the tile-copy waits: with a poll limit of zero every
+    wait of the step gives up at once; the CTAs wait for their copies still
+    in flight, the step reports EVD_ERR_TIMEOUT, the context is destroyed, and
+    a fresh context on the same device still matches the oracle."""
+    make, steps = CASES["box-32x8x8-ternary"]
+    wl = make()
+    sim = _run(evd, wl, 0, precision, evd.EVD_KERNEL_TMA, rows=2)
+    evd.evd_set_wait_limit(sim.ctx, 0)
+    evd.evd_step(sim.ctx, 1)
+    with pytest.raises(evd.EVDError) as ei:
+        evd.evd_check(sim.ctx)
+    assert ei.value.status == evd.EVD_ERR_TIMEOUT
+    assert "gave up" in evd.evd_last_error(sim.ctx)
+    # the default limit back and fresh fields: the same context steps again
+    evd.evd_set_wait_limit(sim.ctx, -1)
+    sim.set_fields(wl.x, wl.n)
+    sim.step(2)
+    sim.check()
+    sim.close()
+    o = oracle_run(wl, steps)
+    fresh = _run(evd, wl, steps, precision, evd.EVD_KERNEL_TMA, rows=2)
+    x = fresh.mole_fractions()
+    assert np.abs(x - o.observables()["x"]).max() < TOL_X[precision]
+    fresh.check()
+    fresh.close()
