@@ -64,11 +64,24 @@ typedef enum { EVD_D2Q9 = 0, EVD_D3Q19 = 1 } evd_lattice;
 
 /* Storage and arithmetic of the populations.
  *   EVD_FP64       double storage, double arithmetic.
- *   EVD_FP32       float storage of the deviation f - w_a rho_ref_i, float
- *                  arithmetic (rho_ref_i = mean initial density of species i).
+ *   EVD_FP32       float storage of deviations, float arithmetic on them, in
+ *                  one of two encodings (evd_set_reference_mode):
+ *                  - one reference per species: f - w_a rho_ref_i with
+ *                    rho_ref_i the mean initial density of species i;
+ *                  - the node's own density: the rest plane holds the
+ *                    species density rho_i(x) and the other planes
+ *                    f_a - w_a rho_i(x); the rest deviation is minus the sum
+ *                    of the others (the deviations of a post-collision state
+ *                    sum to zero), so it costs no extra bytes.  A stencil
+ *                    value from node X enters node O as
+ *                    g(X) + w_a (rho(X) - rho(O)), and the moments and the
+ *                    collision work on deviations from rho(O): a species
+ *                    depleted a thousandfold somewhere keeps the precision of
+ *                    its own density there.
  *   EVD_FP16_STORE half storage of the deviation f - w_a rho~_i(x) from the
  *                  node's own species density, which is stored too (as a
- *                  half, one extra plane per species); float arithmetic.
+ *                  half, one extra plane per species); float arithmetic on
+ *                  deviations from the node's own density, as above.
  *                  Each stored value decodes with the density stored at its
  *                  own node, so interpolation still conserves mass and the
  *                  deviations stay small where densities differ strongly.
@@ -200,9 +213,11 @@ evd_status evd_check(evd_ctx* ctx);
 long long evd_launch_count(const evd_ctx* ctx);
 
 /* Step kernel.  EVD_KERNEL_TMA stages the interpolation stencil of every
- * population plane in shared memory with TMA tile copies (D3Q19, FP32 or
- * FP16 storage, walls in x and y, rows a multiple of 16 bytes); it is the
- * default where it applies.  EVD_KERNEL_GENERAL handles every configuration
+ * population plane in shared memory with TMA tile copies (D3Q19, FP32 with
+ * one reference per species or FP16 storage, walls in x and y, rows a
+ * multiple of 16 bytes); it is the default where it applies (the FP32
+ * node-reference encoding runs the general kernel, and evd_get_kernel then
+ * reports EVD_KERNEL_GENERAL).  EVD_KERNEL_GENERAL handles every configuration
  * (one thread per node, stencil read through the caches).  Both compute the
  * same step.  EVD_KERNEL_AUTO picks the first that applies; asking for
  * EVD_KERNEL_TMA where it does not apply is EVD_ERR_ARG. */
@@ -211,6 +226,21 @@ long long evd_launch_count(const evd_ctx* ctx);
 #define EVD_KERNEL_TMA 2
 evd_status evd_set_kernel(evd_ctx* ctx, int kernel);
 int evd_get_kernel(const evd_ctx* ctx);
+
+/* Reference of the EVD_FP32 encoding (not in the paper; a precision device).
+ * EVD_REF_SPECIES: one reference density per species (the TMA-staged step
+ * implements it).  EVD_REF_NODE: the node's own density (general kernel).
+ * EVD_REF_AUTO (default): per node where some species' density varies by
+ * more than a factor 2 over the initial field, per species otherwise.  The
+ * choice is made by the next evd_set_fields / evd_set_fields_device /
+ * evd_set_populations.  evd_get_reference_mode returns the encoding in
+ * effect: EVD_REF_SPECIES or EVD_REF_NODE for EVD_FP32, EVD_REF_NODE for
+ * EVD_FP16_STORE, EVD_REF_AUTO (0) for EVD_FP64, -1 for a NULL ctx. */
+#define EVD_REF_AUTO 0
+#define EVD_REF_SPECIES 1
+#define EVD_REF_NODE 2
+evd_status evd_set_reference_mode(evd_ctx* ctx, int mode);
+int evd_get_reference_mode(const evd_ctx* ctx);
 
 /* Per-node specific body force field k(x) added to the uniform g:
  * F_i(x) = rho_i (g + k(x)) in the moments, the forcing term and the initial
@@ -281,7 +311,9 @@ evd_status evd_set_wait_limit(evd_ctx* ctx, int polls);
  * FP32/FP16 storage).  Every `every` steps the step kernel also reduces the
  * per-species mass of f_t in double precision; the deficit from the initial
  * masses (the target, computed in double at evd_set_fields) is re-injected in
- * the next step as f_a += w_a (m0_i - m_i)/sites at every node.  0 turns it
+ * the next step in proportion to each node's density, f_a += w_a c_i rho_i(x)
+ * with c_i = (m0_i - m_i)/m_i, so that a species is corrected where it is
+ * present rather than by the same amount at nodes where it is a trace.  0 turns it
  * off.  Default: off for EVD_FP64, every 8 steps for EVD_FP32, every step for
  * EVD_FP16_STORE (its storage rounding drifts the mass faster). */
 evd_status evd_set_mass_correction(evd_ctx* ctx, int every);

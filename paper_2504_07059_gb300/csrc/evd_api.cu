@@ -33,9 +33,16 @@ thread_local std::string g_create_error;
 void evd::set_thread_error(const std::string& msg) { g_create_error = msg; }
 const char* evd::thread_error() { return g_create_error.c_str(); }
 
+// Storage encodings: 0 raw double, 1 float deviations from one reference per
+// species, 2 half deviations from the node's own (half) density, 3 float
+// deviations from the node's own density kept in the rest plane.
+enum : int { ENC_F64 = 0, ENC_F32 = 1, ENC_F16 = 2, ENC_F32N = 3 };
+
 struct evd_ctx {
     HostParams hp;
     int lattice, precision, ns, Q, D;
+    int enc;          // storage encoding in effect (ENC_*)
+    int ref_mode;     // EVD_REF_AUTO / _SPECIES / _NODE (float storage)
     int nx, ny, nz, nsites;
     size_t elem;
     long long pstride;
@@ -54,7 +61,8 @@ struct evd_ctx {
     double* m_target;    // [ns] initial species masses (FP64)
     double* corr[2];     // [ns] per-node mass corrections (two slots)
     unsigned* err_flag;
-    void* small;         // one allocation holding the five arrays above
+    unsigned long long* range;   // [2][ns] min / max species density of an initial field (bits of positive doubles)
+    void* small;         // one allocation holding the six arrays above
     int mc_every;        // mass correction every k steps (0 = off)
     bool tma_ok;         // the TMA-staged step can run this configuration
     int kernel;          // EVD_KERNEL_GENERAL or EVD_KERNEL_TMA
@@ -269,7 +277,33 @@ void set_reference(evd_ctx* c, const double* rho_ref)
 {
     for (int i = 0; i < MAXS; ++i)
         for (int k = 0; k < 3; ++k)
-            c->hp.ref[i][k] = (c->precision != EVD_FP32 || i >= c->ns) ? 0.0 : c->hp.wl[k] * rho_ref[i];
+            c->hp.ref[i][k] = (c->enc != ENC_F32 || i >= c->ns) ? 0.0 : c->hp.wl[k] * rho_ref[i];
+}
+
+// Float storage: deviations from one reference per species (the TMA step
+// implements it) unless a species' density varies by more than a factor
+// kNodeRefContrast over the initial field, where they are taken from each
+// node's own density (a depleted species would otherwise keep the float
+// precision of the species mean, not of its own density).  The caller's
+// choice (evd_set_reference_mode) overrides.  lo / hi: the smallest and
+// largest density of each species over the field.
+constexpr double kNodeRefContrast = 2.0;
+
+void choose_encoding(evd_ctx* c, const double* lo, const double* hi)
+{
+    if (c->precision != EVD_FP32) return;
+    bool node = c->ref_mode == EVD_REF_NODE;
+    if (c->ref_mode == EVD_REF_AUTO)
+        for (int i = 0; i < c->ns; ++i)
+            if (!(hi[i] <= kNodeRefContrast * lo[i])) node = true;
+    c->enc = node ? ENC_F32N : ENC_F32;
+}
+
+// The TMA-staged step runs this context's steps: chosen, a uniform force,
+// and an encoding it implements (not the node-reference float encoding).
+bool tma_active(const evd_ctx* c)
+{
+    return c->kernel == EVD_KERNEL_TMA && !c->kf && c->enc != ENC_F32N;
 }
 
 cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, const double* corr)
@@ -279,7 +313,7 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
     unsigned* e = c->err_flag;
     cudaStream_t st = c->stream;
     c->launches += 1;
-    if (c->kernel == EVD_KERNEL_TMA && !c->kf) {   // the TMA step takes a uniform force only
+    if (tma_active(c)) {
         const int in = (fin == c->buf[0]) ? 0 : 1;
         c->last_parts = c->tma_blocks;
         if (c->precision == EVD_FP32)
@@ -290,22 +324,26 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
     if (h.flags) {   // corrective forcing terms (D2Q9): densities of f_t first when gradients are needed
         if (h.rhof) {
             c->launches += 1;
-            const cudaError_t ed = c->precision == EVD_FP64 ? evd::CorrLaunch<0>::density(h, fin, corr, st)
-                                 : c->precision == EVD_FP32 ? evd::CorrLaunch<1>::density(h, fin, corr, st)
-                                                            : evd::CorrLaunch<2>::density(h, fin, corr, st);
+            const cudaError_t ed = c->enc == ENC_F64  ? evd::CorrLaunch<0>::density(h, fin, corr, st)
+                                 : c->enc == ENC_F32  ? evd::CorrLaunch<1>::density(h, fin, corr, st)
+                                 : c->enc == ENC_F32N ? evd::CorrLaunch<3>::density(h, fin, corr, st)
+                                                      : evd::CorrLaunch<2>::density(h, fin, corr, st);
             if (ed != cudaSuccess) return ed;
         }
-        if (c->precision == EVD_FP64) return evd::CorrLaunch<0>::step(h, fin, fout, mp, e, flags, corr, st);
-        if (c->precision == EVD_FP32) return evd::CorrLaunch<1>::step(h, fin, fout, mp, e, flags, corr, st);
+        if (c->enc == ENC_F64) return evd::CorrLaunch<0>::step(h, fin, fout, mp, e, flags, corr, st);
+        if (c->enc == ENC_F32) return evd::CorrLaunch<1>::step(h, fin, fout, mp, e, flags, corr, st);
+        if (c->enc == ENC_F32N) return evd::CorrLaunch<3>::step(h, fin, fout, mp, e, flags, corr, st);
         return evd::CorrLaunch<2>::step(h, fin, fout, mp, e, flags, corr, st);
     }
-    switch (c->precision * 2 + c->lattice) {
+    switch (c->enc * 2 + c->lattice) {
         case 0: return evd::Launch<0, 0>::step(h, fin, fout, mp, e, flags, corr, st);
         case 1: return evd::Launch<0, 1>::step(h, fin, fout, mp, e, flags, corr, st);
         case 2: return evd::Launch<1, 0>::step(h, fin, fout, mp, e, flags, corr, st);
         case 3: return evd::Launch<1, 1>::step(h, fin, fout, mp, e, flags, corr, st);
         case 4: return evd::Launch<2, 0>::step(h, fin, fout, mp, e, flags, corr, st);
         case 5: return evd::Launch<2, 1>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 6: return evd::Launch<3, 0>::step(h, fin, fout, mp, e, flags, corr, st);
+        case 7: return evd::Launch<3, 1>::step(h, fin, fout, mp, e, flags, corr, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -320,13 +358,15 @@ cudaError_t launch_readout(evd_ctx* c, const void* fin, int flags, double* x, do
     // f_t as the last step saw it includes the correction that step applied
     const double* cr = (!(flags & FLAG_RAW) && c->corr_applied >= 0) ? c->corr[c->corr_applied] : nullptr;
     c->launches += 1;
-    switch (c->precision * 2 + c->lattice) {
+    switch (c->enc * 2 + c->lattice) {
         case 0: return evd::Launch<0, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
         case 1: return evd::Launch<0, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
         case 2: return evd::Launch<1, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
         case 3: return evd::Launch<1, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
         case 4: return evd::Launch<2, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
         case 5: return evd::Launch<2, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 6: return evd::Launch<3, 0>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
+        case 7: return evd::Launch<3, 1>::readout(h, fin, flags, x, rho, u, ui, fpop, mp, e, cr, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -340,13 +380,15 @@ cudaError_t launch_init(evd_ctx* c, const double* x, const double* n, const doub
     unsigned* e = c->err_flag;
     cudaStream_t st = c->stream;
     c->launches += 1;
-    switch (c->precision * 2 + c->lattice) {
+    switch (c->enc * 2 + c->lattice) {
         case 0: return evd::Launch<0, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
         case 1: return evd::Launch<0, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
         case 2: return evd::Launch<1, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
         case 3: return evd::Launch<1, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
         case 4: return evd::Launch<2, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
         case 5: return evd::Launch<2, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 6: return evd::Launch<3, 0>::init(h, x, n, fsrc, prev, cur, mp, e, st);
+        case 7: return evd::Launch<3, 1>::init(h, x, n, fsrc, prev, cur, mp, e, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -355,8 +397,9 @@ cudaError_t launch_init(evd_ctx* c, const double* x, const double* n, const doub
 
 // Fixed-order sum of per-block partials [nblocks][ns]: thread t adds blocks
 // t, t+1024, ... in order, then a fixed binary tree.  Writes the totals to
-// out[ns], or, when target != nullptr, the per-node correction
-// (target_i - total_i) / nsites to out[ns].
+// out[ns], or, when target != nullptr, the relative deficit
+// (target_i - total_i) / total_i that the next step re-injects in proportion
+// to each node's density.
 __global__ void __launch_bounds__(1024)
 evd_k_mass_finish(const double* __restrict__ part, int nblocks, int ns, const double* __restrict__ target,
                   double inv_nsites, double* __restrict__ out)
@@ -371,8 +414,33 @@ evd_k_mass_finish(const double* __restrict__ part, int nblocks, int ns, const do
             if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) out[i] = target ? (target[i] - sm[0]) * inv_nsites : sm[0];
+        if (threadIdx.x == 0) out[i] = target ? (target[i] - sm[0]) / sm[0] : sm[0];
         __syncthreads();
+    }
+}
+
+// Smallest and largest species density x_i M_i n of an initial field,
+// per species: range[i] and range[ns + i] receive the bit patterns of the
+// positive doubles (which order as unsigned integers), by atomic min / max.
+__global__ void __launch_bounds__(128)
+evd_k_field_range(const double* __restrict__ x, const double* __restrict__ nf, int nsites, int ns,
+                  double m0, double m1, double m2, unsigned long long* __restrict__ range)
+{
+    const int node = blockIdx.x * 128 + threadIdx.x;
+    const bool active = node < nsites;
+    const double M[3] = {m0, m1, m2};
+    const double n = active ? (nf ? nf[node] : 1.0) : 1.0;
+    for (int i = 0; i < ns; ++i) {
+        const double v = active ? x[(long long)i * nsites + node] * M[i] * n : 0.0;
+        double lo = active ? v : __longlong_as_double(0x7fefffffffffffffLL), hi = active ? v : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, off));
+            hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(range + i, (unsigned long long)__double_as_longlong(lo));
+            atomicMax(range + ns + i, (unsigned long long)__double_as_longlong(hi));
+        }
     }
 }
 
@@ -614,6 +682,8 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
         }
         c->hp.rhof = c->rhof;
     }
+    c->ref_mode = EVD_REF_AUTO;
+    c->enc = c->precision == EVD_FP64 ? ENC_F64 : c->precision == EVD_FP32 ? ENC_F32 : ENC_F16;
     c->tma_ty = kTmaRows;
     c->tma_ok = tma_setup(c);
     c->kernel = c->tma_ok ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL;
@@ -622,7 +692,7 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
     const int max_tma = c->tma_ok ? evd::TmaLaunch::grid(c->hp, 2) : 0;
     const int max_parts = c->nblocks > max_tma ? c->nblocks : max_tma;
     const size_t part_bytes = ((size_t)max_parts * c->ns * sizeof(double) + 255) / 256 * 256;
-    e = cudaMalloc(&c->small, part_bytes + 5 * 256);
+    e = cudaMalloc(&c->small, part_bytes + 6 * 256);
     if (e != cudaSuccess) {
         if (c->own_bufs) { cudaFree(c->buf[0]); cudaFree(c->buf[1]); }
         delete c;
@@ -634,6 +704,7 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
     c->corr[0] = (double*)((char*)c->small + part_bytes + 512);
     c->corr[1] = (double*)((char*)c->small + part_bytes + 768);
     c->err_flag = (unsigned*)((char*)c->small + part_bytes + 1024);
+    c->range = (unsigned long long*)((char*)c->small + part_bytes + 1280);
     c->corr_pending = c->corr_applied = -1;
     // FP16 storage rounding moves the species mass by ~1e-7 per step on rough
     // fields, so it is corrected every step; FP32 drifts ~1e-9 per step
@@ -717,14 +788,31 @@ evd_status evd_set_fields_device(evd_ctx* c, const double* x_dev, const double* 
     CK(c, cudaGetLastError());
     evd_status s0 = finish_mass(c, c->m_target);
     if (s0 != EVD_OK) return s0;
+    if (c->precision == EVD_FP32 && c->ref_mode == EVD_REF_AUTO) {
+        // the density range of each species decides the float encoding
+        CK(c, cudaMemsetAsync(c->range, 0xff, c->ns * sizeof(unsigned long long), c->stream));
+        CK(c, cudaMemsetAsync(c->range + c->ns, 0, c->ns * sizeof(unsigned long long), c->stream));
+        c->launches += 1;
+        evd_k_field_range<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, c->hp.M[0], c->hp.M[1],
+                                                             c->hp.M[2], c->range);
+        CK(c, cudaGetLastError());
+    }
     if (c->precision != EVD_FP64) {
         double m[MAXS] = {0, 0, 0}, ref[MAXS] = {0, 0, 0};
+        unsigned long long rg[2 * MAXS] = {};
         CK(c, cudaMemcpyAsync(m, c->m_target, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (c->precision == EVD_FP32 && c->ref_mode == EVD_REF_AUTO)
+            CK(c, cudaMemcpyAsync(rg, c->range, 2 * c->ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
+        double lo[MAXS], hi[MAXS];
         for (int i = 0; i < c->ns; ++i) {
             if (!(m[i] > 0.0)) return fail(c, EVD_ERR_ARG, "initial species mass must be > 0");
             ref[i] = m[i] / c->nsites;
+            std::memcpy(&lo[i], &rg[i], sizeof(double));
+            std::memcpy(&hi[i], &rg[c->ns + i], sizeof(double));
         }
+        choose_encoding(c, lo, hi);
         set_reference(c, ref);
     }
     CK(c, cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned), c->stream));
@@ -765,13 +853,24 @@ evd_status evd_set_populations(evd_ctx* c, const double* f_host)
     if (!f_host) return fail(c, EVD_ERR_ARG, "f must not be NULL");
     DeviceGuard dg(c->device);
     const size_t n = (size_t)c->nsites, total = (size_t)c->ns * c->Q * n;
-    double m[MAXS] = {0, 0, 0}, ref[MAXS] = {0, 0, 0};
+    double m[MAXS] = {0, 0, 0}, ref[MAXS] = {0, 0, 0}, lo[MAXS], hi[MAXS];
     for (int i = 0; i < c->ns; ++i) {
-        for (size_t k = 0; k < (size_t)c->Q * n; ++k) m[i] += f_host[(size_t)i * c->Q * n + k];
+        lo[i] = HUGE_VAL;
+        hi[i] = 0.0;
+        for (size_t q = 0; q < n; ++q) {
+            double r = 0.0;
+            for (int a = 0; a < c->Q; ++a) r += f_host[((size_t)i * c->Q + a) * n + q];
+            m[i] += r;
+            lo[i] = std::min(lo[i], r);
+            hi[i] = std::max(hi[i], r);
+        }
         if (!(m[i] > 0.0)) return fail(c, EVD_ERR_ARG, "species mass must be > 0");
         ref[i] = m[i] / n;
     }
-    if (c->precision != EVD_FP64) set_reference(c, ref);
+    if (c->precision != EVD_FP64) {
+        choose_encoding(c, lo, hi);
+        set_reference(c, ref);
+    }
     CK(c, cudaMemcpyAsync(c->m_target, m, c->ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->corr_pending = c->corr_applied = -1;
     evd_status s = ensure_staging(c, total * sizeof(double));
@@ -916,7 +1015,22 @@ evd_status evd_set_kernel(evd_ctx* c, int kernel)
     return EVD_OK;
 }
 
-int evd_get_kernel(const evd_ctx* c) { return c ? (c->kf ? EVD_KERNEL_GENERAL : c->kernel) : 0; }
+int evd_get_kernel(const evd_ctx* c) { return c ? (tma_active(c) ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL) : 0; }
+
+evd_status evd_set_reference_mode(evd_ctx* c, int mode)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (mode != EVD_REF_AUTO && mode != EVD_REF_SPECIES && mode != EVD_REF_NODE)
+        return fail(c, EVD_ERR_ARG, "mode must be EVD_REF_AUTO, EVD_REF_SPECIES or EVD_REF_NODE");
+    c->ref_mode = mode;
+    return EVD_OK;
+}
+
+int evd_get_reference_mode(const evd_ctx* c)
+{
+    if (!c) return -1;
+    return c->enc == ENC_F32N || c->enc == ENC_F16 ? EVD_REF_NODE : c->enc == ENC_F32 ? EVD_REF_SPECIES : EVD_REF_AUTO;
+}
 
 evd_status evd_set_force_field(evd_ctx* c, const double* k_host)
 {

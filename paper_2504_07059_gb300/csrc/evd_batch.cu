@@ -151,7 +151,7 @@ evd_k_batch_finish(const double* __restrict__ part, const MemberInfo* __restrict
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if (lane == 0) {
             double r = 0.0;
-            if (i < mi.ns) r = target ? (target[m * MAXS + i] - s) / (double)mi.sites : s;
+            if (i < mi.ns) r = target ? (target[m * MAXS + i] - s) / s : s;
             out[m * MAXS + i] = r;
         }
     }

@@ -61,11 +61,13 @@ __device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__
         node_force(p, node, gn);
         NodeState<NS, T> s;
         const Nbr nb = neighbours(p, node);
-        gather_all<LAT, NS>(p, fin, node, nb, f);
-        if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
-        store_all<LAT, NS>(p, fout, node, f, s.rho);
+        T R0[NS];
+        node_base<LAT, NS>(p, fin, node, R0);
+        gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+        if (corr) add_correction<LAT, NS>(p, corr, f, R0);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
+        collide<LAT, NS, dev_arith<S>(), false, Codec<S>::NODE>(p, f, s, gn);
+        store_all<LAT, NS>(p, fout, node, f, s.rho, R0);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
     }
@@ -121,14 +123,16 @@ __device__ __noinline__ void item_readout(const Params<T>& p, const MemberInfo& 
         T gn[3];   // specific body force at this node
         node_force(p, node, gn);
         NodeState<NS, T> s;
+        T R0[NS];
+        node_base<LAT, NS>(p, fin, node, R0);
         if (flags & F_RAW) {
             load_raw<LAT, NS>(p, fin, node, f);
         } else {
             const Nbr nb = neighbours(p, node);
-            gather_all<LAT, NS>(p, fin, node, nb, f);
-            if (corr) add_correction<LAT, NS>(p, corr, f);
+            gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+            if (corr) add_correction<LAT, NS>(p, corr, f, R0);
         }
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             if (x) x[mi.xoff + i * n + node] = (double)(s.rho[i] * p.Minv[i]) / (double)s.n;
@@ -200,18 +204,12 @@ __device__ __noinline__ void item_init(const Params<T>& p, const MemberInfo& mi,
                 f[I][A] = p.wl[wclass<LAT>(A)] * r * ((T)1 - (T)0.5 * p.c_inv_cs2[I] * eg);
             });
         });
-        if constexpr (Codec<S>::DARITH)   // float storage computes on deviations
-            static_for<0, NS>([&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                static_for<0, Q>([&](auto ac) {
-                    constexpr int A = decltype(ac)::value;
-                    f[I][A] -= p.ref[I][wclass<LAT>(A)];
-                });
-            });
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
-        store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
-        store_all<LAT, NS>(p, fcur, node, f, s.rho);
+        T R0[NS];
+        to_deviations<LAT, NS, S>(p, f, R0);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
+        store_all<LAT, NS>(p, fprev, node, f, s.rho, R0);
+        collide<LAT, NS, dev_arith<S>(), false, Codec<S>::NODE>(p, f, s, gn);
+        store_all<LAT, NS>(p, fcur, node, f, s.rho, R0);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
     }

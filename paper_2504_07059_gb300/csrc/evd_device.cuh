@@ -192,15 +192,31 @@ inline Params<T> to_params(const HostParams& h)
 
 // --------------------------------------------------------- storage codecs
 // Raw double storage; float storage of the deviation f - w_a rho_ref_i from
-// one reference density per species; half storage of the deviation
-// f - w_a rho~_i(x) from the node's own density rho~_i(x), which is stored
-// (as a half, so exactly) in one extra plane per species.  A stored value at
-// node X decodes with the reference of X itself.
+// one reference density per species; float storage of the deviation from the
+// node's own density (f32n); half storage of the deviation f - w_a rho~_i(x)
+// from the node's own density rho~_i(x), which is stored (as a half, so
+// exactly) in one extra plane per species.  A stored value at node X decodes
+// with the reference of X itself.
+//
+// Flags:
+//   DEV      populations are stored as deviations from a reference
+//   LOCAL    the reference is per node (stored next to the deviations)
+//   DARITH   the moments and the collision work on deviations from one
+//            reference density per species (rref)
+//   NODE     the gather, the moments and the collision work on deviations
+//            from the node's own reference density: a stencil value at X
+//            enters the node O as g(X) + w_a (rho~(X) - rho~(O))
+//   REST_IMPLIED  the rest plane holds the node's density itself; the rest
+//            deviation is minus the sum of the other deviations (the
+//            deviations of a post-collision state sum to zero), so the node
+//            reference costs no extra bytes
 template <typename S> struct Codec;
 template <> struct Codec<double> {
     static constexpr bool DEV = false;
     static constexpr bool LOCAL = false;
     static constexpr bool DARITH = false;
+    static constexpr bool NODE = false;
+    static constexpr bool REST_IMPLIED = false;
     static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
@@ -212,18 +228,71 @@ template <> struct Codec<float> {
     // the full-size populations, whose float rounding would swamp the small
     // momenta and forcing terms of near-rest mixtures
     static constexpr bool DARITH = true;
+    static constexpr bool NODE = false;
+    static constexpr bool REST_IMPLIED = false;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+// Float storage element of the node-reference encoding (same bits as a float).
+struct f32n {
+    float v;
+};
+template <> struct Codec<f32n> {
+    static constexpr bool DEV = true;
+    static constexpr bool LOCAL = true;
+    static constexpr bool DARITH = false;
+    // deviations from the node's own density, which the rest plane holds: a
+    // species depleted a thousandfold somewhere keeps the float precision of
+    // its own density there (one reference per species would spend it on the
+    // mean density)
+    static constexpr bool NODE = true;
+    static constexpr bool REST_IMPLIED = true;
+    static __device__ __forceinline__ float ld(const f32n* p) { return __ldg(reinterpret_cast<const float*>(p)); }
+    static __device__ __forceinline__ void st(f32n* p, float v) { *reinterpret_cast<float*>(p) = v; }
+    static __device__ __forceinline__ float rt(float v) { return v; }
 };
 template <> struct Codec<__half> {
     static constexpr bool DEV = true;
     static constexpr bool LOCAL = true;
     static constexpr bool DARITH = false;
+    static constexpr bool NODE = true;
+    static constexpr bool REST_IMPLIED = false;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
     // the value a float takes once stored
     static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
+
+// Plane holding the node reference densities of species i (node encodings).
+template <int LAT, int NS, typename S>
+__host__ __device__ constexpr int node_ref_plane(int i)
+{
+    return Codec<S>::REST_IMPLIED ? plane_of<LAT, NS>(i, 0) : ref_plane<LAT, NS>(i);
+}
+
+// The densities the deviations of a node are taken from, per species: the
+// node's own stored references (node encodings), the per-species references
+// (DARITH), zero (raw storage).
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void node_base(const Params<T>& p, const S* __restrict__ fin, int node, T (&R)[NS])
+{
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        if constexpr (Codec<S>::NODE)
+            R[i] = (T)Codec<S>::ld(fin + (long long)node_ref_plane<LAT, NS, S>(i) * p.pstride + node);
+        else if constexpr (Codec<S>::DARITH)
+            R[i] = p.rref[i];
+        else
+            R[i] = (T)0;
+    }
+}
+
+// Arithmetic on deviations (from one reference per species, or per node).
+template <typename S>
+__host__ __device__ constexpr bool dev_arith()
+{
+    return Codec<S>::DARITH || Codec<S>::NODE;
+}
 
 // ------------------------------------------------------------- neighbours
 // off[k][o+1]: element offset of the node at o in {-1,0,+1} along dimension k
@@ -265,18 +334,23 @@ __host__ __device__ constexpr int widx(int o, int e) { return o == -e ? 0 : (o =
 // Interior node: f_a(O) = sum over the 1/3/9 stencil nodes O + o of
 // W(o) f*_a(O + o), the tensor product of 1-D weights along the (one or two)
 // dimensions direction a moves in.
+// Storage decodes: raw values (FP64); deviations from one reference per
+// species, interpolated as they are (the weights sum to exactly one); node
+// encodings: the deviation relative to O's own reference R_O,
+// g(X) + w_a (R(X) - R_O), whose interpolant is the deviation of f_a(O)
+// from w_a R_O (R0 = R_O).
 template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __restrict__ fin, int node,
-                                             const Nbr& nb)
+                                             const Nbr& nb, T R0)
 {
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
     const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
-    const S* rplane = fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node;
+    const S* rplane = fin + (long long)node_ref_plane<LAT, NS, S>(I) * p.pstride + node;
     const T wa = p.wl[wclass<LAT>(A)];
-    // the stored value at offset o, decoded with that node's own reference
+    // the stored value at offset o, decoded relative to O's own reference
     // where the storage keeps one per node
     auto ldv = [&](long long o) -> T {
-        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(plane + o));
+        if constexpr (Codec<S>::NODE) return fma(wa, (T)Codec<S>::ld(rplane + o) - R0, (T)Codec<S>::ld(plane + o));
         else return (T)Codec<S>::ld(plane + o);
     };
     T acc;
@@ -316,8 +390,6 @@ __device__ __forceinline__ T gather_interior(const Params<T>& p, const S* __rest
             }
         }
     }
-    // float storage: acc is the deviation g = f - ref itself (the weights sum
-    // to exactly one); half storage decoded every value; FP64 is raw
     return acc;
 }
 
@@ -370,21 +442,21 @@ __device__ __forceinline__ T lumped(const Params<T>& p, int I, const Nbr& nb, bo
 // weight of O's own populations in directions a and its opposite.
 template <int LAT, int NS, int I, int A, typename S, typename T>
 __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict__ fin, int node,
-                                         const Nbr& nb)
+                                         const Nbr& nb, T R0)
 {
     constexpr int ex = ev<LAT>(A, 0), ey = ev<LAT>(A, 1), ez = ev<LAT>(A, 2);
     constexpr int AB = opp<LAT>(A);
     const S* plane = fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node;
-    const S* rplane = fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node;
+    const S* rplane = fin + (long long)node_ref_plane<LAT, NS, S>(I) * p.pstride + node;
     const T wa = p.wl[wclass<LAT>(A)];
-    // float storage gathers deviations; the reference carried by the weights
-    // of this node, ref * (K - 1) with K the sum of the fluid stencil weights
-    // and the lumped ones, is added at the end (K = 1 away from walls)
-    const T ref = (T)0;
+    // deviation storage gathers deviations; the reference carried by the
+    // weights of this node, ref * (K - 1) with K the sum of the fluid stencil
+    // weights and the lumped ones, is added at the end (K = 1 away from walls)
     T ksum = (T)0;
-    // stored value of plane q at offset o, decoded (node reference if kept)
+    // stored value of plane q at offset o, decoded relative to O's reference
+    // where the storage keeps one per node
     auto ldv = [&](const S* q, long long o) -> T {
-        if constexpr (Codec<S>::LOCAL) return fma(wa, (T)Codec<S>::ld(rplane + o), (T)Codec<S>::ld(q + o));
+        if constexpr (Codec<S>::NODE) return fma(wa, (T)Codec<S>::ld(rplane + o) - R0, (T)Codec<S>::ld(q + o));
         else return (T)Codec<S>::ld(q + o);
     };
     T acc = (T)0;
@@ -399,45 +471,79 @@ __device__ __forceinline__ T gather_wall(const Params<T>& p, const S* __restrict
                                    (oz == -1 && nb.lo[2]) || (oz == 1 && nb.hi[2]);
                 if (!solid) {
                     const T w = push_weight<LAT, A>(p, I, -ox, -oy, -oz);  // from O + o to O: d = -o
-                    acc += w * (ldv(plane, nb.off[0][ox + 1] + nb.off[1][oy + 1] + nb.off[2][oz + 1]) + ref);
+                    acc += w * ldv(plane, nb.off[0][ox + 1] + nb.off[1][oy + 1] + nb.off[2][oz + 1]);
                     ksum += w;
                 }
             }
     if constexpr (ex != 0 || ey != 0 || ez != 0) {
         const T ls = lumped<LAT, A>(p, I, nb, true);
         const T lo = lumped<LAT, AB>(p, I, nb, false);
-        if (ls != (T)0) acc += ls * (ldv(plane, 0) + ref);
-        if (lo != (T)0) acc += lo * (ldv(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node, 0) + ref);
+        if (ls != (T)0) acc += ls * ldv(plane, 0);
+        if (lo != (T)0) acc += lo * ldv(fin + (long long)plane_of<LAT, NS>(I, AB) * p.pstride + node, 0);
         ksum += ls + lo;
     }
     if constexpr (Codec<S>::DARITH) acc += p.ref[I][wclass<LAT>(A)] * (ksum - (T)1);
+    if constexpr (Codec<S>::NODE) acc += wa * R0 * (ksum - (T)1);
     return acc;
 }
 
+// Node encodings with the rest plane holding the density: the rest deviation
+// of O is minus the sum of O's stored deviations in the other directions.
+template <int LAT, int NS, int I, typename S, typename T>
+__device__ __forceinline__ T implied_rest(const Params<T>& p, const S* __restrict__ fin, int node)
+{
+    T acc = (T)0;
+    static_for<1, Lat<LAT>::Q>([&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        acc -= (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
+    });
+    return acc;
+}
+
+// f: the gathered populations (raw) or their deviations from R0 (the node's
+// own references, or the per-species ones).
 template <int LAT, int NS, typename S, typename T>
 __device__ __forceinline__ void gather_all(const Params<T>& p, const S* __restrict__ fin, int node,
-                                           const Nbr& nb, T (&f)[NS][Lat<LAT>::Q])
+                                           const Nbr& nb, const T (&R0)[NS], T (&f)[NS][Lat<LAT>::Q])
 {
     constexpr int Q = Lat<LAT>::Q;
+    constexpr int A0 = Codec<S>::REST_IMPLIED ? 1 : 0;
+    if constexpr (Codec<S>::REST_IMPLIED)
+        static_for<0, NS>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            f[I][0] = implied_rest<LAT, NS, I>(p, fin, node);
+        });
     if (!nb.any_wall) {
         static_for<0, NS>([&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            static_for<0, Q>([&](auto ac) {
+            static_for<A0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_interior<LAT, NS, I, A>(p, fin, node, nb);
+                f[I][A] = gather_interior<LAT, NS, I, A>(p, fin, node, nb, R0[I]);
             });
         });
     } else {
         static_for<0, NS>([&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            static_for<0, Q>([&](auto ac) {
+            static_for<A0, Q>([&](auto ac) {
                 constexpr int A = decltype(ac)::value;
-                f[I][A] = gather_wall<LAT, NS, I, A>(p, fin, node, nb);
+                f[I][A] = gather_wall<LAT, NS, I, A>(p, fin, node, nb, R0[I]);
             });
         });
     }
 }
 
+// Raw storage (no references): the gather of the double-precision step.
+template <int LAT, int NS, typename T>
+__device__ __forceinline__ void gather_all(const Params<T>& p, const double* __restrict__ fin, int node,
+                                           const Nbr& nb, T (&f)[NS][Lat<LAT>::Q])
+{
+    const T R0[NS] = {};
+    gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+}
+
+// The stored state of the node itself (no streaming), decoded as the gather
+// decodes: raw values, deviations from the per-species references, or
+// deviations from the node's own references R0.
 template <int LAT, int NS, typename S, typename T>
 __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict__ fin, int node,
                                          T (&f)[NS][Lat<LAT>::Q])
@@ -447,32 +553,35 @@ __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict
         constexpr int I = decltype(ic)::value;
         static_for<0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
-            T v = (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
-            if constexpr (Codec<S>::LOCAL)
-                v = fma(p.wl[wclass<LAT>(A)], (T)Codec<S>::ld(fin + (long long)ref_plane<LAT, NS>(I) * p.pstride + node), v);
-            f[I][A] = v;   // float storage: the deviation itself
+            if constexpr (Codec<S>::REST_IMPLIED && A == 0)
+                f[I][0] = implied_rest<LAT, NS, I>(p, fin, node);
+            else
+                f[I][A] = (T)Codec<S>::ld(fin + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node);
         });
     });
 }
 
-// rho: the node's species densities, the references of half storage (stored
-// rounded to half, and the deviations taken from that rounded value).
+// Store the post-collision state f (raw, or deviations from R0).  rho: the
+// node's species densities.  Node encodings store the new reference
+// R* = rho (rounded as stored: half storage keeps it as a half) and the
+// deviations from it, g - w_a (R* - R0) (R* - R0 is exact: both are close).
 template <int LAT, int NS, typename S, typename T>
 __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fout, int node,
-                                          const T (&f)[NS][Lat<LAT>::Q], const T (&rho)[NS])
+                                          const T (&f)[NS][Lat<LAT>::Q], const T (&rho)[NS], const T (&R0)[NS])
 {
     constexpr int Q = Lat<LAT>::Q;
     static_for<0, NS>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        [[maybe_unused]] T rr = (T)0;
-        if constexpr (Codec<S>::LOCAL) {
-            rr = (T)Codec<S>::rt((float)rho[I]);
-            Codec<S>::st(fout + (long long)ref_plane<LAT, NS>(I) * p.pstride + node, (float)rr);
+        [[maybe_unused]] T dR = (T)0;
+        if constexpr (Codec<S>::NODE) {
+            const T rr = (T)Codec<S>::rt((float)rho[I]);
+            dR = rr - R0[I];
+            Codec<S>::st(fout + (long long)node_ref_plane<LAT, NS, S>(I) * p.pstride + node, (float)rr);
         }
-        static_for<0, Q>([&](auto ac) {
+        static_for<Codec<S>::REST_IMPLIED ? 1 : 0, Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             T v = f[I][A];
-            if constexpr (Codec<S>::LOCAL) v -= p.wl[wclass<LAT>(A)] * rr;   // float: already a deviation
+            if constexpr (Codec<S>::NODE) v -= p.wl[wclass<LAT>(A)] * dR;
             Codec<S>::st(fout + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node, v);
         });
     });
@@ -531,11 +640,13 @@ struct NodeState {
 // the cross relaxation rates 1/tau_ij of Eq. (relation_tauij_diff_coeff):
 // Eq. (Luo&Girimaji_tau) for two species and the Sec. 4.1 closed forms for
 // three, written for 1/tau_ij.
-// DA: f holds deviations g = f - ref (float storage): rho_i = rref_i + sum g,
-// j_i = sum e g (the references cancel in j).
+// DA: f holds deviations g = f - w R0 (deviation storage): rho_i = R0_i +
+// sum g, j_i = sum e g (the references cancel in j); R0 is the per-species
+// reference or the node's own (node_base).
 template <int LAT, int NS, bool DA = false, typename T>
 __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat<LAT>::Q],
-                                        NodeState<NS, T>& s, unsigned& err, const T (&g)[3])
+                                        NodeState<NS, T>& s, unsigned& err, const T (&g)[3],
+                                        const T* R0 = nullptr)
 {
     constexpr int Q = Lat<LAT>::Q;
     s.rho_mix = (T)0;
@@ -555,7 +666,7 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
             if constexpr (ev<LAT>(A, 2) == -1) j[2] -= v;
         });
         s.drho[I] = r;
-        if constexpr (DA) r = p.rref[I] + r;
+        if constexpr (DA) r = R0[I] + r;
         if (!(r > (T)0)) err |= ERR_RHO;
         const T rinv = (T)1 / r;
         s.rho[I] = r;
@@ -624,7 +735,9 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 // DA: f holds deviations g = f - ref and receives g* = f* - ref, written so
 // that only the last addition is at the size of g:
 //   g* = g + (w drho + refc - g)/tau + w rho (phi B + b) + (1 - 1/(2 tau)) S
-// (1 - 1/tau = omt exactly on the float grid of the constants)
+// (1 - 1/tau = omt exactly on the float grid of the constants); refc, the
+// rounding of the per-species reference, is zero for a node reference
+// (NODE: ref = w R0 exactly, so w rho - ref = w drho).
 // with feq = w rho (1 + phi), phi = t1 (1 + t1/2) - u^2/(2 c_s^2),
 //      B = 1/tau + b, b = (e-u).a / c_s^2 (the same algebra as above, minus ref).
 // CORR: add the corrective terms of Eq. (improved_forcing_scheme) that
@@ -634,7 +747,7 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 //   S_p    = w [(e e - cs2 I)/cs2^2 . u] . grad(rho_i cs2)      (subtracted),
 //   S_rho  = w [(e e - cs2 I)/cs2 . u_i^eq] . (w_i grad rho),   w_i = rho_i/rho;
 // grad: [NS + 1][3] lattice gradients of rho_i and rho at this node.
-template <int LAT, int NS, bool DA = false, bool CORR = false, typename T>
+template <int LAT, int NS, bool DA = false, bool CORR = false, bool NODE = false, typename T>
 __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
                                         const NodeState<NS, T>& s, const T (&g)[3],
                                         const T (*grad)[3] = nullptr)
@@ -671,7 +784,8 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             wr[i][c] = p.wl[c] * s.rho[i];
-            if constexpr (DA) dt[i][c] = fma(p.wl[c], s.drho[i], p.refc[i][c]);   // w rho - ref
+            if constexpr (DA && NODE) dt[i][c] = p.wl[c] * s.drho[i];                   // w rho - ref
+            else if constexpr (DA) dt[i][c] = fma(p.wl[c], s.drho[i], p.refc[i][c]);
         }
         sr[i] = s.rho[i] * p.inv_cs2[i] * p.sfac[i];
     }
@@ -784,15 +898,25 @@ __device__ __forceinline__ void block_mass(const T (&rho)[NS], bool active, doub
 
 // ----------------------------------------------------------------- kernels
 // One time step: gather f*_{t-1} -> f_t, collide -> f*_t.
-// Uniform re-injection of a species-mass deficit: f_a += w_a * corr_i keeps
-// the moments' shape and adds corr_i to rho_i at every node.
+// Re-injection of a species-mass deficit in proportion to the local density:
+// corr_i = (m0_i - m_i) / m_i (the FP64 totals), and every node adds
+// corr_i rho_i(x) to its density as f_a += w_a corr_i rho_i(x), which keeps
+// the moments' shape.  A trace species thus receives (or loses) mass where it
+// is abundant, in proportion to what its rounding can have lost there,
+// instead of the same amount at every node.  R0: the references the
+// deviations f are taken from (rho_i = R0_i + sum_a f_a).
 template <int LAT, int NS, typename T>
 __device__ __forceinline__ void add_correction(const Params<T>& p, const double* __restrict__ corr,
-                                               T (&f)[NS][Lat<LAT>::Q])
+                                               T (&f)[NS][Lat<LAT>::Q], const T (&R0)[NS])
 {
     static_for<0, NS>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        const T ci = (T)__ldg(corr + I);
+        T r = R0[I];
+        static_for<0, Lat<LAT>::Q>([&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            r += f[I][A];
+        });
+        const T ci = (T)__ldg(corr + I) * r;
         static_for<0, Lat<LAT>::Q>([&](auto ac) {
             constexpr int A = decltype(ac)::value;
             f[I][A] = fma(p.wl[wclass<LAT>(A)], ci, f[I][A]);
@@ -807,6 +931,7 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
        const double* __restrict__ corr)
 {
     constexpr int Q = Lat<LAT>::Q;
+    constexpr bool DA = dev_arith<S>();
     const int node = blockIdx.x * BLOCK + threadIdx.x;
     const bool active = node < p.nsites;
     T f[NS][Q];
@@ -816,11 +941,13 @@ k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
     unsigned err = 0;
     if (active) {
         const Nbr nb = neighbours(p, node);
-        gather_all<LAT, NS>(p, fin, node, nb, f);
-        if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
-        store_all<LAT, NS>(p, fout, node, f, s.rho);
+        T R0[NS];
+        node_base<LAT, NS>(p, fin, node, R0);
+        gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+        if (corr) add_correction<LAT, NS>(p, corr, f, R0);
+        moments<LAT, NS, DA>(p, f, s, err, gn, R0);
+        collide<LAT, NS, DA, false, Codec<S>::NODE>(p, f, s, gn);
+        store_all<LAT, NS>(p, fout, node, f, s.rho, R0);
         if (err) atomicOr(err_flag, err);
     }
     if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
@@ -837,15 +964,17 @@ k_density(const Params<T> p, const S* __restrict__ fin, T* __restrict__ rhof, co
     if (node >= p.nsites) return;
     T f[NS][Q];
     const Nbr nb = neighbours(p, node);
-    gather_all<LAT, NS>(p, fin, node, nb, f);
-    if (corr) add_correction<LAT, NS>(p, corr, f);
+    T R0[NS];
+    node_base<LAT, NS>(p, fin, node, R0);
+    gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+    if (corr) add_correction<LAT, NS>(p, corr, f, R0);
     T mix = (T)0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         T r = (T)0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) r += f[i][a];
-        if constexpr (Codec<S>::DARITH) r = p.rref[i] + r;
+        if constexpr (dev_arith<S>()) r = R0[i] + r;
         rhof[(long long)i * p.nsites + node] = r;
         mix += r;
     }
@@ -894,15 +1023,17 @@ k_step_corr(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
     unsigned err = 0;
     if (active) {
         const Nbr nb = neighbours(p, node);
-        gather_all<LAT, NS>(p, fin, node, nb, f);
-        if (corr) add_correction<LAT, NS>(p, corr, f);
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        T R0[NS];
+        node_base<LAT, NS>(p, fin, node, R0);
+        gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+        if (corr) add_correction<LAT, NS>(p, corr, f, R0);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
         T grad[NS + 1][3] = {};
         if (p.rhof)   // only the gradient terms (S_p, S_rho) have a density field
 #pragma unroll
             for (int i = 0; i <= NS; ++i) lattice_grad<LAT>(p, nb, p.rhof + (long long)i * p.nsites, node, grad[i]);
-        collide<LAT, NS, Codec<S>::DARITH, true>(p, f, s, gn, grad);
-        store_all<LAT, NS>(p, fout, node, f, s.rho);
+        collide<LAT, NS, dev_arith<S>(), true, Codec<S>::NODE>(p, f, s, gn, grad);
+        store_all<LAT, NS>(p, fout, node, f, s.rho, R0);
         if (err) atomicOr(err_flag, err);
     }
     if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
@@ -926,14 +1057,16 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
     NodeState<NS, T> s;
     unsigned err = 0;
     if (active) {
+        T R0[NS];
+        node_base<LAT, NS>(p, fin, node, R0);
         if (flags & F_RAW) {
             load_raw<LAT, NS>(p, fin, node, f);
         } else {
             const Nbr nb = neighbours(p, node);
-            gather_all<LAT, NS>(p, fin, node, nb, f);
-            if (corr) add_correction<LAT, NS>(p, corr, f);   // as the last step saw f_t
+            gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+            if (corr) add_correction<LAT, NS>(p, corr, f, R0);   // as the last step saw f_t
         }
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
         const long long ns_ = p.nsites;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -953,12 +1086,45 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
                 for (int a = 0; a < Q; ++a) {
                     double v = (double)f[i][a];
                     if constexpr (Codec<S>::DARITH) v += (double)p.ref[i][wclass<LAT>(a)];
+                    if constexpr (Codec<S>::NODE) v += (double)p.wl[wclass<LAT>(a)] * (double)R0[i];
                     fpop[(i * Q + a) * ns_ + node] = v;
                 }
         }
         if (err) atomicOr(err_flag, err);
     }
     block_mass<NS>(s.rho, active, mass_part);
+}
+
+// Full-size populations of a node (the initial state) into the arithmetic of
+// the storage: R0 receives the references (the node's own densities for the
+// node encodings, rounded as stored; the per-species references for DARITH;
+// zero for raw storage) and f the deviations from them.
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void to_deviations(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q], T (&R0)[NS])
+{
+    constexpr int Q = Lat<LAT>::Q;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        if constexpr (Codec<S>::NODE) {
+            T r = (T)0;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) r += f[i][a];
+            R0[i] = (T)Codec<S>::rt((float)r);
+        } else if constexpr (Codec<S>::DARITH) {
+            R0[i] = p.rref[i];
+        } else {
+            R0[i] = (T)0;
+        }
+    }
+    if constexpr (dev_arith<S>())
+        static_for<0, NS>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            static_for<0, Q>([&](auto ac) {
+                constexpr int A = decltype(ac)::value;
+                if constexpr (Codec<S>::NODE) f[I][A] -= p.wl[wclass<LAT>(A)] * R0[I];
+                else f[I][A] -= p.ref[I][wclass<LAT>(A)];
+            });
+        });
 }
 
 // Initial state f_0 into fprev (kept for the time-0 readout) and its collision
@@ -998,18 +1164,12 @@ k_init(const Params<T> p, const double* __restrict__ xf, const double* __restric
                 });
             });
         }
-        if constexpr (Codec<S>::DARITH)   // float storage computes on deviations
-            static_for<0, NS>([&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                static_for<0, Q>([&](auto ac) {
-                    constexpr int A = decltype(ac)::value;
-                    f[I][A] -= p.ref[I][wclass<LAT>(A)];
-                });
-            });
-        moments<LAT, NS, Codec<S>::DARITH>(p, f, s, err, gn);
-        store_all<LAT, NS>(p, fprev, node, f, s.rho);
-        collide<LAT, NS, Codec<S>::DARITH>(p, f, s, gn);
-        store_all<LAT, NS>(p, fcur, node, f, s.rho);
+        T R0[NS];
+        to_deviations<LAT, NS, S>(p, f, R0);
+        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
+        store_all<LAT, NS>(p, fprev, node, f, s.rho, R0);
+        collide<LAT, NS, dev_arith<S>(), false, Codec<S>::NODE>(p, f, s, gn);
+        store_all<LAT, NS>(p, fcur, node, f, s.rho, R0);
         if (err) atomicOr(err_flag, err);
     }
     block_mass<NS>(s.rho, active, mass_part);

@@ -168,34 +168,40 @@ struct TmaMaps {
 // z-moving groups (and node densities) for the halo planes zb-1 and ze.
 __device__ __forceinline__ bool stage_is_halo(int k, int zb, int ze) { return k < zb || k >= ze; }
 
-// masked 1-D weights of one in-plane dimension for a direction component e
-// (+1 -> index 0, -1 -> index 1): solid stencil nodes get weight zero
-struct MaskedW {
-    float w[2][3];
-    float sum[2];
+// ------------------------------------------------------ packed float pairs
+// The two members of an opposite-direction pair (A, A + 1 in the library's
+// D3Q19 order) go through the same operations; f32x2 instructions issue both
+// at once.  Their rounding is that of the scalar operations.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// 1-D weights of source offset o (-1, 0, 1) for a pair whose first member
+// moves in +e (first = true) or -e: WP[o + 1] = (W for +e, W for -e) with
+// W(o; e) = w[widx(o, e)]; for the pair led by -e the members swap.
+struct WPair {
+    float2 w[3];   // (w[widx(o, +1)], w[widx(o, -1)]) at index o + 1
 };
 
-__device__ __forceinline__ MaskedW masked_weights(const float (&w)[3], bool lo, bool hi)
+__device__ __forceinline__ WPair weight_pairs(const float (&w)[3])
 {
-    MaskedW m;
-#pragma unroll
-    for (int ei = 0; ei < 2; ++ei) {
-        const int e = ei == 0 ? 1 : -1;
-        float s = 0.0f;
-#pragma unroll
-        for (int o = -1; o <= 1; ++o) {
-            const bool solid = (o == -1 && lo) || (o == 1 && hi);
-            const float v = solid ? 0.0f : w[o == -e ? 0 : (o == 0 ? 1 : 2)];
-            m.w[ei][o + 1] = v;
-            s += v;
-        }
-        m.sum[ei] = s;
-    }
-    return m;
+    WPair p;
+    p.w[0] = make_float2(w[0], w[2]);
+    p.w[1] = make_float2(w[1], w[1]);
+    p.w[2] = make_float2(w[2], w[0]);
+    return p;
+}
+
+template <int e>
+__device__ __forceinline__ float2 wpo(const WPair& p, int o)
+{
+    return e > 0 ? p.w[o + 1] : p.w[1 - o];
 }
 
 // Half storage: the stored densities rho~ of the 3x3 in-plane neighbourhood of
-// the thread's node in this stage (group 7, which carries the x and y halo).
+// the thread's node in this stage (group 7, which carries the x and y halo;
+// nodes beyond a wall read as zero, the fill of the tile copy).
 template <int NS, typename S, int TY, int SLOTS>
 __device__ __forceinline__ void dens_block(const unsigned char* slot, int sp, int tx, int ty, float (&rd)[3][3])
 {
@@ -208,66 +214,66 @@ __device__ __forceinline__ void dens_block(const unsigned char* slot, int sp, in
         for (int ox = 0; ox < 3; ++ox) rd[oy][ox] = (float)r[(ty + oy) * W7 + tx + G::XP - 1 + ox];
 }
 
-// rho~ interpolated with the in-plane stencil (and masked weights) of the
-// directions whose in-plane components are (ex, ey).  A half population is
-// g + w_a rho~ at every stencil node, so by linearity its interpolant is the
-// interpolant of g plus w_a times this one, which every direction with the
-// same (ex, ey) shares (up to three in D3Q19).
+// rho~ interpolated with the in-plane stencil of the directions whose
+// in-plane components are (ex, ey).  A half population is g + w_a rho~ at
+// every stencil node, so by linearity its interpolant is the interpolant of
+// g plus w_a times this one, which every direction with the same (ex, ey)
+// shares (up to three in D3Q19).
 template <int ex, int ey>
-__device__ __forceinline__ float dens_interp(const float (&rd)[3][3], const MaskedW& mx, const MaskedW& my)
+__device__ __forceinline__ float dens_interp(const float (&rd)[3][3], const float (&w)[3])
 {
-    constexpr int xi = ex > 0 ? 0 : 1, yi = ey > 0 ? 0 : 1;
     auto row = [&](int oy) -> float {
         if constexpr (ex == 0) return rd[oy][1];
-        else return mx.w[xi][0] * rd[oy][0] + mx.w[xi][1] * rd[oy][1] + mx.w[xi][2] * rd[oy][2];
+        else return w[widx(1, ex)] * rd[oy][2] + (w[widx(0, ex)] * rd[oy][1] + w[widx(-1, ex)] * rd[oy][0]);
     };
     if constexpr (ey == 0) return row(1);
-    else return my.w[yi][0] * row(0) + my.w[yi][1] * row(1) + my.w[yi][2] * row(2);
+    else return w[widx(1, ey)] * row(2) + (w[widx(0, ey)] * row(1) + w[widx(-1, ey)] * row(0));
 }
 
-// In-plane interpolation of direction A: float storage interpolates the
+// In-plane interpolation of the pair (A, A + 1) of one slab: the 1, 3 or 3x3
+// points of Eq. Second_order_spatial_interpolation in the slab's plane, the
+// two members' planes being adjacent in the stage.  A stencil node beyond a
+// wall holds zero (the tile copy's fill), so the full weights act as the
+// weights of the fluid nodes alone.  Float storage interpolates the
 // deviations from its reference as they are (the reference carried by the
-// weights is added at wall nodes only, through K - 1); half storage
-// interpolates the stored g and adds wa times dI, the interpolated node
-// densities of the direction's stencil (dens_interp).
+// weights is added at wall nodes only, through K - 1); half storage adds
+// w_a times dI, the interpolated node densities of each member's stencil.
 template <int A, int NS, typename S, int TY, int SLOTS>
-__device__ __forceinline__ float inplane(const unsigned char* slot, int sp, int tx, int ty, const MaskedW& mx,
-                                         const MaskedW& my, float dI, float wa)
+__device__ __forceinline__ float2 inplane2(const unsigned char* slot, int sp, int tx, int ty, const WPair& wp,
+                                           float2 dI, float wa)
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1);
     constexpr int g = grp<1>(A);
     constexpr int cls = grp_cls(g);
     constexpr int W = G::bw(cls);
-    constexpr int xi = ex > 0 ? 0 : 1, yi = ey > 0 ? 0 : 1;
-    const S* s = reinterpret_cast<const S*>(slot + G::group_offset(g)) +
-                 (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
+    constexpr int PE = G::plane_elems(g);
+    static_assert(grp_pos<1>(A + 1) == grp_pos<1>(A) + 1 && opp<1>(A) == A + 1, "pair planes must be adjacent");
+    const S* s = reinterpret_cast<const S*>(slot + G::group_offset(g)) + (sp * grp_size(g) + grp_pos<1>(A)) * PE;
     const int cx = tx + ((cls & 1) ? G::XP : 0);
     const int cy = ty + ((cls & 2) ? 1 : 0);
-    auto ld = [&](int yy, int xx) -> float { return (float)s[yy * W + xx]; };
-    float v;
+    auto ld = [&](int yy, int xx) -> float2 {
+        return make_float2((float)s[yy * W + xx], (float)s[PE + yy * W + xx]);
+    };
+    auto xrow = [&](int yy) -> float2 {
+        return pfma(wpo<ex>(wp, 1), ld(yy, cx + 1), pfma(wpo<ex>(wp, 0), ld(yy, cx), pmul(wpo<ex>(wp, -1), ld(yy, cx - 1))));
+    };
+    float2 v;
     if constexpr (cls == 0) {
         v = ld(cy, cx);
     } else if constexpr (cls == 1) {
-        v = mx.w[xi][0] * ld(cy, cx - 1) + mx.w[xi][1] * ld(cy, cx) + mx.w[xi][2] * ld(cy, cx + 1);
+        v = xrow(cy);
     } else if constexpr (cls == 2) {
-        v = my.w[yi][0] * ld(cy - 1, cx) + my.w[yi][1] * ld(cy, cx) + my.w[yi][2] * ld(cy + 1, cx);
+        v = pfma(wpo<ey>(wp, 1), ld(cy + 1, cx), pfma(wpo<ey>(wp, 0), ld(cy, cx), pmul(wpo<ey>(wp, -1), ld(cy - 1, cx))));
     } else {
-        float acc = 0.0f;
-#pragma unroll
-        for (int oy = -1; oy <= 1; ++oy) {
-            const float row = mx.w[xi][0] * ld(cy + oy, cx - 1) + mx.w[xi][1] * ld(cy + oy, cx) +
-                              mx.w[xi][2] * ld(cy + oy, cx + 1);
-            acc += my.w[yi][oy + 1] * row;
-        }
-        v = acc;
+        v = pfma(wpo<ey>(wp, 1), xrow(cy + 1), pfma(wpo<ey>(wp, 0), xrow(cy), pmul(wpo<ey>(wp, -1), xrow(cy - 1))));
     }
-    if constexpr (G::LOCAL) return fmaf(wa, dI, v);
+    if constexpr (G::LOCAL) return pfma(bc2(wa), dI, v);
     else return v;
 }
 
-// Unit lattice speed off the walls: weights (1, 0, 0), the upstream node
-// (half storage: dI is that node's density rho~).
+// Unit lattice speed: weights (1, 0, 0), each member's upstream node (half
+// storage: dI is that node's density rho~); a node beyond a wall reads zero.
 template <int A, int NS, typename S, int TY, int SLOTS>
 __device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp, int tx, int ty, float dI, float wa)
 {
@@ -284,6 +290,13 @@ __device__ __forceinline__ float inplane_unit(const unsigned char* slot, int sp,
     else return (float)s[cy * W + cx];
 }
 
+// e_A . v for the unit vector of direction A, starting from its first term
+template <int A>
+__device__ __forceinline__ float edot3(const float (&v)[3])
+{
+    return edot<1, A>(v);
+}
+
 template <int NS, typename S, int TY, int SLOTS>
 __global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
@@ -293,6 +306,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 {
     using G = TmaLayout<NS, S, TY, SLOTS>;
     constexpr int Q = 19;
+    constexpr int NP = 9;   // opposite-direction pairs (2k + 1, 2k + 2)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     float4* exch = reinterpret_cast<float4*>(smem + G::ring_bytes);
@@ -331,7 +345,8 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const int slot = idx % SLOTS;
         const int k = kfirst + idx;
         const bool halo = stage_is_halo(k, zb, ze);
-        const int zc = zwall ? k : (k % p.nz + p.nz) % p.nz;   // walled: out of range -> zero fill
+        // walled z: a slab beyond the wall is out of range and reads as zero
+        const int zc = zwall ? k : (k % p.nz + p.nz) % p.nz;
         if (lane == 0) mbar_arrive_expect_tx(full(slot), (unsigned)G::stage_bytes(halo));
         if (!halo || gz) tma_load_4d(ring + (unsigned)(slot * G::slot_bytes) + goff, &maps.m[g], gcx, gcy, zc, gc3,
                                      full(slot));
@@ -347,22 +362,25 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     float w[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) w[a] = p.w1[sp][a];
+    const WPair wp = weight_pairs(w);
     const float csp = p.c[sp], inv_cs2 = p.inv_cs2[sp], c_inv_cs2 = p.c_inv_cs2[sp];
-    const float tau_inv = p.tau_inv[sp], omt = p.omt[sp], sfac = p.sfac[sp];
+    const float tau_inv = p.tau_inv[sp], omt = p.omt[sp];
+    const float isf = inv_cs2 * p.sfac[sp];
     const bool xlo = p.wall[0] && x == 0, xhi = p.wall[0] && x == p.nx - 1;
     const bool ylo = p.wall[1] && y == 0, yhi = p.wall[1] && y == p.ny - 1;
     const bool col_wall = xlo || xhi || ylo || yhi;
-    const MaskedW mx = masked_weights(w, xlo, xhi), my = masked_weights(w, ylo, yhi);
-    const bool unit_fast = p.unit[sp] && !col_wall;
+    const bool unit = p.unit[sp] != 0;   // the same for the whole warp
     const int nxy = p.nx * p.ny;
     const int pstride = (int)p.pstride;   // the host guarantees planes * pstride < 2^31
     const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
+    const bool want_mass = (flags & F_MASS) != 0;
 
-    // running sums: z-moving directions (A: node at z = k-1, B: node at k),
-    // in-plane directions (N: value at z = k-1)
-    float accA[Q], accB[Q], accN[Q];
+    // running sums, per pair k: z-moving pairs (A: node at z = k-1, B: node
+    // at k), in-plane pairs and the rest (N: value at z = k-1)
+    float2 accA[NP], accB[NP], accN[NP];
+    float accN0 = 0.0f;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) accA[a] = accB[a] = accN[a] = 0.0f;
+    for (int k = 0; k < NP; ++k) accA[k] = accB[k] = accN[k] = make_float2(0.0f, 0.0f);
     double mass_acc = 0.0;
     unsigned err = 0;
     bool failed = false;
@@ -378,13 +396,12 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         }
         const unsigned char* base = smem + slot * G::slot_bytes;
         const bool halo = stage_is_halo(k, zb, ze);
-        const bool solid_slab = zwall && (k < 0 || k >= p.nz);
         const int zo = k - 1;                   // node finished this iteration
         const bool emit = zo >= zb && zo < ze;  // the same for every thread of the CTA
         const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
         const int node = x + p.nx * y + nxy * zo;
         const bool wall_node = emit && active && (col_wall || zlo || zhi);
-        float f[Q], cen[Q], cenr = 0.0f;
+        float cen[Q], cenr = 0.0f;
         if (wall_node) {
             // the node's own post-collision populations, for the App. A terms:
             // float storage copies them to shared memory without holding
@@ -401,26 +418,60 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
         }
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1), wait_polls);
+        // float storage: the App. A terms of a wall node, from its own
+        // populations (copied to shared memory at the top of the iteration),
+        // replace them there now, while few registers are live; they join the
+        // gathered values once those are formed
+        const float4* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
+        if constexpr (G::CEN_SMEM) {
+            if (wall_node) {
+                cp_async_wait_all();
+                float* cw = reinterpret_cast<float*>(smem + G::cen_offset) + threadIdx.x;
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    constexpr int A = 2 * K + 1, B = A + 1;
+                    const float ref = p.ref[sp][wclass<1>(A)];
+                    const float4 la = __ldg(L + A), lb = __ldg(L + B);
+                    const float ca = cw[A * G::threads], cb = cw[B * G::threads];
+                    cw[A * G::threads] = la.x * ca + la.y * cb + ref * la.z;
+                    cw[B * G::threads] = lb.x * cb + lb.y * ca + ref * lb.z;
+                });
+            }
+        }
         // half storage: this stage's node densities around the node (the
         // density term of every stencil is taken from them once per stage)
         float rd[3][3] = {};
         if constexpr (G::LOCAL)
             if (ok) dens_block<NS, S, TY, SLOTS>(base, sp, tx, ty, rd);
-        if (ok && unit_fast) {
-            static_for<0, Q>([&](auto ac) {
-                constexpr int A = decltype(ac)::value;
+        float f0;
+        float2 F[NP];
+        if (ok && unit) {
+            // exact shift: each member reads its upstream node; a z-moving
+            // member bound for +z takes slab z - 1 (two iterations ago, held
+            // in the shift register accB -> accA), one bound for -z slab z + 1
+            f0 = accN0;
+            if (!halo) accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1][1], p.wl[0]);
+            static_for<0, NP>([&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                constexpr int A = 2 * K + 1, B = A + 1;
                 constexpr int ez = ev<1>(A, 2);
-                const float dI = rd[1 - ev<1>(A, 1)][1 - ev<1>(A, 0)], wa = p.wl[wclass<1>(A)];
+                const float wa = p.wl[wclass<1>(A)];
+                const float dA = rd[1 - ev<1>(A, 1)][1 - ev<1>(A, 0)], dB = rd[1 - ev<1>(B, 1)][1 - ev<1>(B, 0)];
                 if constexpr (ez == 0) {
-                    f[A] = accN[A];
-                    if (!halo) accN[A] = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
-                } else if constexpr (ez > 0) {
-                    // exact shift: node z takes slab z - 1, which arrived two iterations ago
-                    f[A] = accA[A];
-                    accA[A] = accB[A];
-                    accB[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
-                } else {
-                    f[A] = solid_slab ? 0.0f : inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dI, wa);
+                    F[K] = accN[K];
+                    if (!halo)
+                        accN[K] = make_float2(inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa),
+                                              inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa));
+                } else if constexpr (ez > 0) {   // A bound for +z, B for -z
+                    F[K].x = accA[K].x;
+                    accA[K].x = accB[K].x;
+                    accB[K].x = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa);
+                    F[K].y = inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa);
+                } else {                         // A bound for -z, B for +z
+                    F[K].y = accA[K].y;
+                    accA[K].y = accB[K].y;
+                    accB[K].y = inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa);
+                    F[K].x = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa);
                 }
             });
         } else if (ok) {
@@ -428,22 +479,28 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
             if constexpr (G::LOCAL)
                 static_for<0, 9>([&](auto kc) {
                     constexpr int K = decltype(kc)::value;
-                    di[K / 3][K % 3] = dens_interp<K % 3 - 1, K / 3 - 1>(rd, mx, my);
+                    di[K / 3][K % 3] = dens_interp<K % 3 - 1, K / 3 - 1>(rd, w);
                 });
-            static_for<0, Q>([&](auto ac) {
-                constexpr int A = decltype(ac)::value;
-                constexpr int ez = ev<1>(A, 2);
-                const float dI = di[ev<1>(A, 1) + 1][ev<1>(A, 0) + 1], wa = p.wl[wclass<1>(A)];
+            f0 = accN0;
+            if (!halo) {
+                if constexpr (G::LOCAL) accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1][1], p.wl[0]);
+                else accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, 0.0f, 0.0f);
+            }
+            static_for<0, NP>([&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                constexpr int A = 2 * K + 1;
+                constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1), ez = ev<1>(A, 2);
+                const float wa = p.wl[wclass<1>(A)];
+                const float2 dI = make_float2(di[ey + 1][ex + 1], di[1 - ey][1 - ex]);
                 if constexpr (ez == 0) {
-                    f[A] = accN[A];
-                    if (!halo) accN[A] = inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, dI, wa);
+                    F[K] = accN[K];
+                    if (!halo) accN[K] = inplane2<A, NS, S, TY, SLOTS>(base, sp, tx, ty, wp, dI, wa);
                 } else {
-                    const float R =
-                        solid_slab ? 0.0f : inplane<A, NS, S, TY, SLOTS>(base, sp, tx, ty, mx, my, dI, wa);
+                    const float2 R = inplane2<A, NS, S, TY, SLOTS>(base, sp, tx, ty, wp, dI, wa);
                     // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
-                    f[A] = accA[A] + w[widx(1, ez)] * R;
-                    accA[A] = accB[A] + w[widx(0, ez)] * R;
-                    accB[A] = w[widx(-1, ez)] * R;
+                    F[K] = pfma(wpo<ez>(wp, 1), R, accA[K]);
+                    accA[K] = pfma(wpo<ez>(wp, 0), R, accB[K]);
+                    accB[K] = pmul(wpo<ez>(wp, -1), R);
                 }
             });
         }
@@ -452,47 +509,56 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float rho = 1.0f, drho = 0.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
         if (ok && emit) {
             if (wall_node) {
-                if constexpr (G::CEN_SMEM) cp_async_wait_all();
-                const float* cs = reinterpret_cast<const float*>(smem + G::cen_offset) + threadIdx.x;
-                const float4* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
-                static_for<1, Q>([&](auto ac) {
-                    constexpr int A = decltype(ac)::value;
-                    constexpr int AB = opp<1>(A);
-                    const float4 l = __ldg(L + A);
-                    if constexpr (G::LOCAL) {
+                if constexpr (G::CEN_SMEM) {
+                    const float* cs = reinterpret_cast<const float*>(smem + G::cen_offset) + threadIdx.x;
+                    static_for<0, NP>([&](auto kc) {
+                        constexpr int K = decltype(kc)::value;
+                        constexpr int A = 2 * K + 1;
+                        F[K] = padd(F[K], make_float2(cs[A * G::threads], cs[(A + 1) * G::threads]));
+                    });
+                } else {   // half storage: own populations in registers, decoded with their node density
+                    static_for<0, NP>([&](auto kc) {
+                        constexpr int K = decltype(kc)::value;
+                        constexpr int A = 2 * K + 1, B = A + 1;
                         const float wa = p.wl[wclass<1>(A)];
-                        f[A] += l.x * fmaf(wa, cenr, cen[A]) + l.y * fmaf(wa, cenr, cen[AB]);
-                    } else {   // deviations, plus the reference the weights carry
-                        float ca, cb;
-                        if constexpr (G::CEN_SMEM) { ca = cs[A * G::threads]; cb = cs[AB * G::threads]; }
-                        else { ca = cen[A]; cb = cen[AB]; }
-                        f[A] += l.x * ca + l.y * cb + p.ref[sp][wclass<1>(A)] * l.z;
-                    }
-                });
+                        const float4 la = __ldg(L + A), lb = __ldg(L + B);
+                        const float ca = fmaf(wa, cenr, cen[A]), cb = fmaf(wa, cenr, cen[B]);
+                        F[K].x += la.x * ca + la.y * cb;
+                        F[K].y += lb.x * cb + lb.y * ca;
+                    });
+                }
             }
-            if (corr) {
-                const float ci = (float)__ldg(corr + sp);
-                static_for<0, Q>([&](auto ac) {
-                    constexpr int A = decltype(ac)::value;
-                    f[A] = fmaf(p.wl[wclass<1>(A)], ci, f[A]);
-                });
-            }
-            // sums started from their first term (no explicit 0 + x)
-            float r = f[0], j[3];
-            static_for<1, Q>([&](auto ac) {
-                constexpr int A = decltype(ac)::value;
-                r += f[A];
+            // moments from the pairs: s = f_A + f_B adds to rho, d = f_A - f_B
+            // to the momentum along A's components (sums start from a term)
+            float r = f0, j[3];
+            static_for<0, NP>([&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                constexpr int A = 2 * K + 1;
+                const float sK = F[K].x + F[K].y, dK = F[K].x - F[K].y;
+                r += sK;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     constexpr int first[3] = {first_dir<1>(0), first_dir<1>(1), first_dir<1>(2)};
                     const int e = ev<1>(A, d);
-                    if (A == first[d]) j[d] = e > 0 ? f[A] : -f[A];
-                    else if (e == 1) j[d] += f[A];
-                    else if (e == -1) j[d] -= f[A];
+                    if (A == first[d]) j[d] = e > 0 ? dK : -dK;
+                    else if (e == 1) j[d] += dK;
+                    else if (e == -1) j[d] -= dK;
                 }
             });
             drho = r;
-            if constexpr (Codec<S>::DARITH) r = p.rref[sp] + r;
+            if (corr) {
+                // mass correction in proportion to the node's density: f_a +=
+                // w_a ci (ci = corr rho), which adds ci to rho and no momentum
+                const float ci = (float)__ldg(corr + sp) * (Codec<S>::DARITH ? p.rref[sp] + r : r);
+                drho += ci;
+                f0 = fmaf(p.wl[0], ci, f0);
+                const float2 c1 = bc2(p.wl[1] * ci), c2 = bc2(p.wl[2] * ci);
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    F[K] = padd(F[K], wclass<1>(2 * K + 1) == 1 ? c1 : c2);
+                });
+            }
+            r = Codec<S>::DARITH ? p.rref[sp] + drho : drho;
             if (active && !(r > 0.0f)) err |= ERR_RHO;
             rho = r;
             const float rinv = __fdividef(1.0f, r);
@@ -520,16 +586,16 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 #pragma unroll
         for (int i = 1; i < NS; ++i)
             if (i == sp) { rho = r[i]; ueq[0] = ue[i][0]; ueq[1] = ue[i][1]; ueq[2] = ue[i][2]; }
-        float rho_m = 0.0f, n = 0.0f;
+        float rho_m = r[0], n = r[0] * p.Minv[0];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) { rho_m += r[i]; n += r[i] * p.Minv[i]; }
+        for (int i = 1; i < NS; ++i) { rho_m += r[i]; n = fmaf(r[i], p.Minv[i], n); }
         const float rinv_m = __fdividef(1.0f, rho_m);
         float u[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            float acc = 0.0f;
+            float acc = r[0] * ue[0][d];
 #pragma unroll
-            for (int i = 0; i < NS; ++i) acc += r[i] * ue[i][d];
+            for (int i = 1; i < NS; ++i) acc = fmaf(r[i], ue[i][d], acc);
             u[d] = acc * rinv_m;
         }
         float X[MAXS][MAXS] = {};
@@ -555,93 +621,89 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 #pragma unroll
             for (int jj = i + 1; jj < NS; ++jj)
                 if (active && (!(X[i][jj] > 0.0f) || !isfinite(X[i][jj]))) err |= ERR_TAU;
+        // this thread's row of 1/tau_ij, weighted by rho_j / rho
+        float xr[NS];
+#pragma unroll
+        for (int jj = 0; jj < NS; ++jj) {
+            float xs = X[0][jj];
+#pragma unroll
+            for (int i = 1; i < NS; ++i) xs = (i == sp) ? X[i][jj] : xs;
+            xr[jj] = (jj == sp) ? 0.0f : r[jj] * xs * rinv_m;
+        }
         float V[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            float acc = 0.0f;
+            float acc = xr[0] * (ueq[d] - ue[0][d]);
 #pragma unroll
-            for (int jj = 0; jj < NS; ++jj) {
-                float xs = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NS; ++i) xs = (i == sp) ? X[i][jj] : xs;
-                if (jj != sp) acc += r[jj] * xs * (ueq[d] - ue[jj][d]);
-            }
-            V[d] = acc * rinv_m;
+            for (int jj = 1; jj < NS; ++jj) acc = fmaf(xr[jj], ueq[d] - ue[jj][d], acc);
+            V[d] = acc;
         }
 
-        // ---- collision of this species (same algebra as the general kernel)
-        const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const float ug = u[0] * p.g[0] + u[1] * p.g[1] + u[2] * p.g[2];
-        float av[3], ua = 0.0f;
+        // ---- collision of this species (Eq. LBE_forcing), pairs at a time.
+        // With t = c e.u/cs^2, b = c e.a/cs^2 (a = (u^eq - u)/tau - V),
+        // gam = c e.g, all odd in e, and P = t^2/2 + U2 even, a pair (A, -A)
+        // updates as  f*_+- = omt f_+- + E +- O  with
+        //   half  (f):  E = w rho (P T + t b) + K (gam t - u.g),
+        //               O = w rho (t T + b P) + K gam,
+        //               T = 1/tau - (u.a)/cs^2, U2 = 1 - u^2/(2 cs^2);
+        //   float (deviations g = f - ref):
+        //               E = w rho (P T + t b + Bm) + K (gam t - u.g) + (w drho + refc)/tau,
+        //               O = w rho (t T + b (P + 1)) + K gam,
+        //               Bm = -(u.a)/cs^2, U2 = -u^2/(2 cs^2);
+        //   K = w rho (1 - 1/(2 tau))/cs^2.
+        constexpr bool DA = Codec<S>::DARITH;
+        float av[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            av[d] = (ueq[d] - u[d]) * tau_inv - V[d];
-            ua += u[d] * av[d];
-        }
-        constexpr bool DA = Codec<S>::DARITH;   // float: the deviation form of the general kernel
-        const float Bc = tau_inv - inv_cs2 * ua;
+        for (int d = 0; d < 3; ++d) av[d] = fmaf(ueq[d] - u[d], tau_inv, -V[d]);
+        const float ua = fmaf(u[2], av[2], fmaf(u[1], av[1], u[0] * av[0]));
+        const float usq = fmaf(u[2], u[2], fmaf(u[1], u[1], u[0] * u[0]));
+        const float ug = fmaf(u[2], p.g[2], fmaf(u[1], p.g[1], u[0] * p.g[0]));
         const float Bm = -inv_cs2 * ua;
-        const float U2 = DA ? -0.5f * inv_cs2 * usq : 1.0f - 0.5f * inv_cs2 * usq;
-        float dt[3] = {0.0f, 0.0f, 0.0f};
-        if constexpr (DA)
+        const float T = tau_inv + Bm;
+        const float U2 = DA ? -0.5f * inv_cs2 * usq : fmaf(-0.5f * inv_cs2, usq, 1.0f);
+        float U[3], Av[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dt[c] = fmaf(p.wl[c], drho, p.refc[sp][c]);   // w rho - ref
-        const float wr[3] = {p.wl[0] * rho, p.wl[1] * rho, p.wl[2] * rho};
-        const float sr = rho * inv_cs2 * sfac;
-        if (active) mass_acc += (double)rho;
+        for (int d = 0; d < 3; ++d) { U[d] = c_inv_cs2 * u[d]; Av[d] = c_inv_cs2 * av[d]; }
+        const float sr = rho * isf;
+        float wr[3], Kc[3], Cc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            wr[c] = p.wl[c] * rho;
+            Kc[c] = p.wl[c] * sr;
+            const float dtt = DA ? fmaf(p.wl[c], drho, p.refc[sp][c]) * tau_inv : 0.0f;   // (w rho - ref)/tau
+            Cc[c] = fmaf(-Kc[c], ug, dtt);
+        }
+        if (active && want_mass) mass_acc += (double)rho;
         // half storage: the node density, rounded as stored, is the reference
         float rr = 0.0f;
         if constexpr (G::LOCAL) {
             rr = Codec<S>::rt(rho);
             if (active) Codec<S>::st(fout + (ref_plane<1, NS>(sp) * pstride + node), rr);
         }
-        // Directions in opposite pairs (A, -A): with t1 = c e.u / c_s^2 and e.a,
-        // e.g odd in e, each update is f + (even part) +- (odd part), the parts
-        // formed once per pair.  Float (deviations):
-        //   g* = g + (w rho - ref - g)/tau + w rho X + S,  X = phi (1/tau + b) + b,
-        //   phi = t1 + t1^2/2 + U2, b = c/cs2 e.a + Bm, S = K (c e.g (1 + t1) - u.g);
-        // half: f* = omt f + w rho (phi B) + S, B = c/cs2 e.a + Bc.
-        const float cg[3] = {csp * p.g[0], csp * p.g[1], csp * p.g[2]};
-        const float tB = DA ? tau_inv + Bm : Bc;
-        auto emit_store = [&](int A, int C, float fs) {
+        auto store = [&](int A, int C, float fs) {
             if (active) {
                 if constexpr (G::LOCAL) Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs - p.wl[C] * rr);
                 else Codec<S>::st(fout + (plane_of<1, NS>(sp, A) * pstride + node), fs);
             }
         };
-        static_for<0, Q>([&](auto ac) {
-            constexpr int A = decltype(ac)::value;
-            constexpr int AB = opp<1>(A);
+        {   // rest: t = b = gam = 0
+            const float XE0 = DA ? fmaf(U2, T, Bm) : U2 * T;
+            store(0, 0, fmaf(omt, f0, fmaf(wr[0], XE0, Cc[0])));
+        }
+        static_for<0, NP>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            constexpr int A = 2 * K + 1;
             constexpr int C = wclass<1>(A);
-            const float K = p.wl[C] * sr;
-            if constexpr (A == 0) {
-                // rest: t1 = e.a = e.g = 0
-                const float S0 = -K * ug;
-                float fs;
-                if constexpr (DA) fs = f[0] + fmaf(tau_inv, dt[0] - f[0], fmaf(wr[0], fmaf(U2, tB, Bm), S0));
-                else fs = fmaf(omt, f[0], fmaf(wr[0] * U2, Bc, S0));
-                emit_store(0, 0, fs);
-            } else if constexpr (A < AB) {
-                const float t1 = c_inv_cs2 * edot<1, A>(u);
-                const float bO = c_inv_cs2 * edot<1, A>(av);
-                const float ceg = edot<1, A>(cg);
-                const float phiE = fmaf(0.5f * t1, t1, U2);
-                // even and odd parts of X (float) or of phi B (half)
-                const float XE = DA ? fmaf(phiE, tB, fmaf(t1, bO, Bm)) : fmaf(phiE, tB, t1 * bO);
-                const float XO = DA ? fmaf(t1, tB, fmaf(phiE, bO, bO)) : fmaf(t1, tB, phiE * bO);
-                const float E = fmaf(wr[C], XE, K * fmaf(ceg, t1, -ug));
-                const float O = fmaf(wr[C], XO, K * ceg);
-                float fa, fb;
-                if constexpr (DA) {   // g* directly: one large addition per direction
-                    fa = f[A] + fmaf(tau_inv, dt[C] - f[A], E + O);
-                    fb = f[AB] + fmaf(tau_inv, dt[C] - f[AB], E - O);
-                } else {
-                    fa = fmaf(omt, f[A], E + O);
-                    fb = fmaf(omt, f[AB], E - O);
-                }
-                emit_store(A, C, fa);
-                emit_store(AB, C, fb);
-            }
+            const float t = edot3<A>(U), b = edot3<A>(Av), gam = csp * edot3<A>(p.g);
+            const float P = fmaf(0.5f * t, t, U2);
+            const float XE = DA ? fmaf(P, T, fmaf(t, b, Bm)) : fmaf(P, T, t * b);
+            const float XO = DA ? fmaf(t, T, fmaf(b, P, b)) : fmaf(t, T, b * P);
+            const float Kg = Kc[C] * gam;
+            const float E = fmaf(wr[C], XE, fmaf(Kg, t, Cc[C]));
+            const float O = fmaf(wr[C], XO, Kg);
+            const float2 fs = pfma(bc2(omt), F[K], pfma(make_float2(1.0f, -1.0f), bc2(O), bc2(E)));
+            store(A, C, fs.x);
+            store(A + 1, C, fs.y);
         });
     }
 
@@ -664,7 +726,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         return;
     }
     if (err) atomicOr(err_flag, err);
-    if (flags & F_MASS) {
+    if (want_mass) {
         // per-species block partial over the TY warps of a species, fixed order
         double v = mass_acc;
 #pragma unroll

@@ -25,6 +25,7 @@ EVD_MAX_SPECIES = 3
 EVD_KERNEL_AUTO, EVD_KERNEL_GENERAL, EVD_KERNEL_TMA = 0, 1, 2
 EVD_ADJOINT_REVERSE, EVD_ADJOINT_DUAL = 0, 1
 EVD_FORCE_S_DIFF, EVD_FORCE_S_P, EVD_FORCE_S_RHO = 1, 2, 4
+EVD_REF_AUTO, EVD_REF_SPECIES, EVD_REF_NODE = 0, 1, 2
 
 STATUS_NAMES = {0: "EVD_OK", 1: "EVD_ERR_ARG", 2: "EVD_ERR_CUDA", 3: "EVD_ERR_UNSTABLE",
                 4: "EVD_ERR_TIMEOUT", 5: "EVD_ERR_STATE"}
@@ -90,6 +91,8 @@ _SIGNATURES = {
     "evd_loss_gradient": (_st, [_vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
     "evd_set_wait_limit": (_st, [_vp, ctypes.c_int]),
+    "evd_set_reference_mode": (_st, [_vp, ctypes.c_int]),
+    "evd_get_reference_mode": (ctypes.c_int, [_vp]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
     "evd_destroy": (_st, [_vp]),
@@ -325,6 +328,14 @@ def evd_set_mass_correction(ctx, every: int):
 
 def evd_set_wait_limit(ctx, polls: int):
     _check(lib().evd_set_wait_limit(ctx, int(polls)), ctx)
+
+
+def evd_set_reference_mode(ctx, mode: int):
+    _check(lib().evd_set_reference_mode(ctx, int(mode)), ctx)
+
+
+def evd_get_reference_mode(ctx) -> int:
+    return lib().evd_get_reference_mode(ctx)
 
 
 def evd_get_target_mass(ctx, out):
