@@ -181,6 +181,25 @@ def gpu_device_id(torch, dev: int) -> str | None:
     return None
 
 
+def oracle_all_cores():
+    """Context for timing the oracle on every host core: its OpenMP build
+    (bitwise the serial arithmetic) where the compiler has OpenMP, else the
+    serial build.  Yields the number of threads a step runs on."""
+    import contextlib
+
+    from oracle import oracle as O
+
+    @contextlib.contextmanager
+    def ctx():
+        so = O.build_omp()
+        if so is None:
+            yield O.threads()
+            return
+        with O.swapped_library(so):
+            yield O.threads()
+    return ctx()
+
+
 def time_oracle_sample(side: int, steps: int, warmup: int = 0) -> tuple[float, int, float]:
     """The FP64 oracle on a side^3 copy of the stratification workload (same
     recipe and seed).  Returns (seconds for ``steps`` steps, species-site
@@ -197,15 +216,27 @@ def time_oracle_sample(side: int, steps: int, warmup: int = 0) -> tuple[float, i
     return dt, wl.ns * wl.nsites * steps, dt / max(steps, 1)
 
 
-def cpu_baseline(budget_s: float = 15.0) -> dict:
-    """Bounded sample of the oracle: 32^3 copy of the workload, as many steps
-    as fit in about budget_s seconds (at least 2)."""
-    dt1, _, per = time_oracle_sample(32, 1)
+def _oracle_rate(side: int, budget_s: float) -> tuple[float, int, float]:
+    """(GLUPS, steps, seconds) of the oracle on a side^3 copy, as many steps as
+    fit in about budget_s seconds (at least 2)."""
+    _, _, per = time_oracle_sample(side, 1)
     steps = max(2, int(budget_s / max(per, 1e-6)))
-    dt, ssu, _ = time_oracle_sample(32, steps)
-    return {"value": ssu / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"stratification-d3q19-32x32x32 (same recipe and seed), {steps} steps, FP64, "
-                      f"single-threaded C, {dt:.1f} s"}
+    dt, ssu, _ = time_oracle_sample(side, steps)
+    return ssu / dt / 1e9, steps, dt
+
+
+def cpu_baseline(budget_s: float = 10.0) -> dict:
+    """Bounded samples of the oracle on the 32^3 copy of the workload: on
+    every host core (the OpenMP build), and single-threaded beside it."""
+    with oracle_all_cores() as threads:
+        v_all, steps_all, dt_all = _oracle_rate(32, budget_s)
+    v_one, steps_one, dt_one = _oracle_rate(32, budget_s)
+    sample = "stratification-d3q19-32x32x32 (same recipe and seed), FP64 C oracle"
+    return {"value": v_all, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": f"{sample}, {steps_all} steps on {threads} threads (OpenMP), {dt_all:.1f} s",
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": f"{sample}, {steps_one} steps single-threaded, {dt_one:.1f} s"}}
 
 
 def time_oracle_tubes(budget_s: float, steps: int | None = None, warmup: int = 0) -> tuple[float, int, str]:
@@ -244,31 +275,33 @@ def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload == "tubes":
-        # bounded: each step a pass over as many tubes as fit in ~60 s / (W + K)
-        dt, ssu, what = time_oracle_tubes(60.0 / (args.steps + args.warmup) * args.steps)
-        value = ssu / dt / 1e9
-        ssu_step = sum(t.ns * t.nsites for t in W.batched_tubes())
-        out = {
-            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ssu_step / (value * 1e9) * 1e3,   # one step of the whole sweep at this rate
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(tubes_config(), precision="fp64", sample=what),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }
-        print(json.dumps(out), flush=True)
-        return
-    # choose the sample cube so that warmup + steps end within about a minute
-    _, _, per16 = time_oracle_sample(16, 1)
-    total = args.steps + args.warmup
-    side = 16
-    for s in (32, 24, 16, 12, 8):
-        if per16 * (s / 16.0) ** 3 * total <= 60.0:
-            side = s
-            break
-    dt, ssu, _ = time_oracle_sample(side, args.steps, args.warmup)
+    with oracle_all_cores() as threads:
+        if args.workload == "tubes":
+            # bounded: each step a pass over as many tubes as fit in ~60 s / (W + K)
+            dt, ssu, what = time_oracle_tubes(60.0 / (args.steps + args.warmup) * args.steps)
+            value = ssu / dt / 1e9
+            what = what.replace("single-threaded", f"{threads} thread(s)")
+            ssu_step = sum(t.ns * t.nsites for t in W.batched_tubes())
+            out = {
+                "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ssu_step / (value * 1e9) * 1e3,   # one step of the whole sweep at this rate
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(tubes_config(), precision="fp64", sample=what),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            }
+            print(json.dumps(out), flush=True)
+            return
+        # choose the sample cube so that warmup + steps end within about a minute
+        _, _, per16 = time_oracle_sample(16, 1)
+        total = args.steps + args.warmup
+        side = 16
+        for s in (48, 40, 32, 24, 16, 12, 8):
+            if per16 * (s / 16.0) ** 3 * total <= 60.0:
+                side = s
+                break
+        dt, ssu, _ = time_oracle_sample(side, args.steps, args.warmup)
     value = ssu / dt / 1e9
     wl = make_workload(args.workload, args.size)
     out = {
@@ -279,9 +312,9 @@ def run_reference(args) -> None:
         "data": "synthetic",
         "config": dict(wl.describe(), precision="fp64",
                        sample=f"{side}x{side}x{side} copy of the workload (same recipe and seed)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "nproc": os.cpu_count(),
                          "sample": f"stratification-d3q19-{side}^3, {args.steps} steps after {args.warmup} "
-                                   f"warm-up, FP64 single-threaded C oracle"},
+                                   f"warm-up, FP64 C oracle on {threads} thread(s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -306,69 +339,73 @@ def replica_throughput(ms_local: float, ssu_rank: int, device) -> tuple[float, f
 def tubes_config(members: int = 512) -> dict:
     return {"workload": f"batched-tubes-d2q9-{members}x32", "lattice": "D2Q9", "members": members, "width": 32,
             "length": "log-uniform [128, 4096]", "species": "2 or 3", "mass_ratio": "U[1, 10]",
+            "diffusivity": "binary members U[0.01, 0.1]; ternary members U[0.06, 0.1] (narrowed from "
+                           "U[0.01, 0.1]: ternary tubes with a mass ratio near 10 and D_ij below ~0.05 "
+                           "diverge in the FP64 oracle itself)",
             "walls": ["y-", "y+"], "seed": W.SEED}
 
 
-def run_tubes(args, torch, dev, world, rank, local) -> None:
-    """The batched sweep: 512 independent tubes advanced by one persistent
-    launch per step, replayed from CUDA graphs, schedule picked by the
-    autotuner before the timed region."""
+def measure_tubes(torch, dev, stream, prec: str, steps: int, warmup: int, members: int = 512,
+                  schedule: str = "", e2e: bool = True, fp64: bool = True, sync=None) -> dict:
+    """The batched sweep: ``members`` independent tubes advanced by one
+    persistent launch per step, replayed from CUDA graphs, schedule picked by
+    the autotuner (or given) before the timed region.  ``sync`` runs around
+    the timed region (the ranks' barrier)."""
     from paper_2504_07059_gb300 import evd
-    tubes = W.batched_tubes()[:args.members]
-    prec = args.precision
-    stream = torch.cuda.current_stream(dev)
+    sync = sync or (lambda: None)
+    tubes = W.batched_tubes()[:members]
     b = evd.Batch(tubes, prec, stream)
     x_all = np.concatenate([t.x.ravel() for t in tubes])
     evd.evd_batch_set_fields(b.b, x_all)   # host path once, for the mass targets
     t0 = time.perf_counter()
-    if args.schedule:
-        sched = tuple(int(v) for v in args.schedule.split(","))
+    if schedule:
+        sched = tuple(int(v) for v in schedule.split(","))
         evd.evd_batch_set_schedule(b.b, *sched)
     else:
         sched = evd.evd_batch_autotune(b.b, 8)
     tune_s = time.perf_counter() - t0
     ssu_step = sum(t.ns * t.nsites for t in tubes)
     bpl = sum(t.ns * t.nsites * bytes_per_ssu(t, prec) for t in tubes)
-    evd.evd_batch_step(b.b, args.warmup)
+    evd.evd_batch_step(b.b, warmup)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    sync()
     torch.cuda.synchronize(dev)
     launches0 = evd.evd_batch_launch_count(b.b)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_device_id(torch, local)) as clocks:
-        start.record(stream)
-        evd.evd_batch_step(b.b, args.steps)
-        stop.record(stream)
-        torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    start.record(stream)
+    evd.evd_batch_step(b.b, steps)
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    sync()
     torch.cuda.synchronize(dev)
     ms = start.elapsed_time(stop)
     evd.evd_batch_check(b.b)
     launches = evd.evd_batch_launch_count(b.b) - launches0
-    ms_max, value = replica_throughput(ms, ssu_step * args.steps, dev)
     peak, peak_kind = measured_peaks()
-    achieved = bpl / (ms / args.steps * 1e-3) / 1e9
-
-    # end to end through the public API: upload the initial mole fractions
-    # from pinned host memory, run the steps, read the mole fractions back
-    x_host = torch.from_numpy(x_all).pin_memory()
-    out_host = torch.empty_like(x_host).pin_memory()
-    e2e_times = []
-    for _ in range(0 if args.no_e2e else 2):
-        torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
-        evd.evd_batch_set_fields(b.b, x_host.data_ptr())
-        evd.evd_batch_step(b.b, args.steps)
-        evd.evd_batch_get_mole_fractions(b.b, out_host.data_ptr())
-        e2e_times.append(time.perf_counter() - t1)
-    e2e_s = min(e2e_times) if e2e_times else float("nan")
-    _, e2e_value = replica_throughput(e2e_s * 1e3, ssu_step * args.steps, dev)
+    achieved = bpl / (ms / steps * 1e-3) / 1e9
+    res = {"ms": ms, "ms_per_step": ms / steps, "ssu_step": ssu_step, "bytes_per_launch": bpl,
+           "value": ssu_step * steps / (ms * 1e-3) / 1e9, "achieved": achieved, "peak": peak,
+           "peak_source": peak_kind, "frac": achieved / peak, "launches": launches,
+           "schedule": {"item_sites": sched[0], "ctas_per_sm": sched[1],
+                        "autotune_s": None if schedule else tune_s}}
+    if e2e:
+        # end to end through the public API: upload the initial mole fractions
+        # from pinned host memory, run the steps, read the mole fractions back
+        x_host = torch.from_numpy(x_all).pin_memory()
+        out_host = torch.empty_like(x_host).pin_memory()
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            evd.evd_batch_set_fields(b.b, x_host.data_ptr())
+            evd.evd_batch_step(b.b, steps)
+            evd.evd_batch_get_mole_fractions(b.b, out_host.data_ptr())
+            times.append(time.perf_counter() - t1)
+        res["e2e_s"] = min(times)
+        res["h2d"] = x_host.numel() * 8
+        res["d2h"] = out_host.numel() * 8
     b.close()
-
-    fp64 = None
-    if prec != "fp64" and not args.no_fp64:
+    if fp64 and prec != "fp64":
         b64 = evd.Batch(tubes, "fp64", stream)
         evd.evd_batch_set_fields(b64.b, x_all)
         evd.evd_batch_step(b64.b, 8)
@@ -382,41 +419,83 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
         evd.evd_batch_check(b64.b)
         ms64 = a.elapsed_time(z) / n64
         b64.close()
-        fp64 = {"ms_per_step": ms64, "value": ssu_step / (ms64 * 1e-3) / 1e9, "unit": UNIT, "steps": n64,
-                "speedup": ms64 / (ms / args.steps)}
+        res["fp64"] = {"ms_per_step": ms64, "value": ssu_step / (ms64 * 1e-3) / 1e9, "unit": UNIT, "steps": n64,
+                       "speedup": ms64 / (ms / steps)}
+    return res
 
+
+def run_tubes(args, torch, dev, world, rank, local) -> None:
+    """The batched sweep as the bench's workload (one JSON line)."""
+    stream = torch.cuda.current_stream(dev)
+    sync = (lambda: torch.distributed.barrier()) if world > 1 else None
+    with ClockSampler(gpu_device_id(torch, local)) as clocks:
+        r = measure_tubes(torch, dev, stream, args.precision, args.steps, args.warmup, args.members, args.schedule,
+                          e2e=not args.no_e2e, fp64=not args.no_fp64, sync=sync)
+    ms_max, value = replica_throughput(r["ms"], r["ssu_step"] * args.steps, dev)
+    e2e_value = float("nan")
+    if "e2e_s" in r:
+        _, e2e_value = replica_throughput(r["e2e_s"] * 1e3, r["ssu_step"] * args.steps, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, ssu, what = time_oracle_tubes(15.0)
-        cpu = {"value": ssu / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what}
+        with oracle_all_cores() as threads:
+            dt, ssu, what = time_oracle_tubes(15.0)
+        cpu = {"value": ssu / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": what.replace("single-threaded", f"{threads} thread(s)")}
     if rank == 0:
+        prec = args.precision
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)"}[prec],
             "data": "synthetic",
-            "config": dict(tubes_config(len(tubes)), precision=prec, parallelism=f"replicas{world}",
-                           schedule={"item_sites": sched[0], "ctas_per_sm": sched[1],
-                                     "autotune_s": None if args.schedule else tune_s},
-                           graph_steps=8, l2="inputs larger than L2 (no flush needed)"),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                         "kernel": "k_step_batch", "bytes_per_launch": bpl,
+            "config": dict(tubes_config(args.members), precision=prec, parallelism=f"replicas{world}",
+                           schedule=r["schedule"], graph_steps=8, l2="inputs larger than L2 (no flush needed)"),
+            "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
+                         "frac": r["frac"], "traffic": None, "peak_source": r["peak_source"],
+                         "kernel": "k_step_batch", "bytes_per_launch": r["bytes_per_launch"],
                          "timing": "CUDA events around the timed steps, divided by the steps "
                                    "(includes the small mass-correction reductions)"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": x_host.numel() * 8,
-                    "d2h_bytes_per_step": out_host.numel() * 8, "steps_per_e2e_step": args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r.get("h2d", 0),
+                    "d2h_bytes_per_step": r.get("d2h", 0), "steps_per_e2e_step": args.steps,
                     "what": "evd_batch_set_fields(pinned host x) + evd_batch_step(steps) + "
                             "evd_batch_get_mole_fractions(pinned host)"},
-            "gpu_launches": launches,
+            "gpu_launches": r["launches"],
             "clocks": clocks.summary(),
         }
-        if fp64 is not None:
-            out["vs_fp64_gpu"] = fp64
+        if "fp64" in r:
+            out["vs_fp64_gpu"] = r["fp64"]
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)
+
+
+def measure_single(torch, dev, stream, wl, prec: str, x_dev, steps: int, warmup: int) -> dict:
+    """One lattice in another storage: CUDA-event time per step over ``steps``
+    steps after ``warmup``, the roofline of its step kernel (algorithmic bytes
+    of that storage) and the kernel that ran."""
+    from paper_2504_07059_gb300 import evd
+    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, prec, stream)
+    evd.evd_set_fields_device(sim.ctx, x_dev, None)
+    evd.evd_step(sim.ctx, warmup)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    evd.evd_step(sim.ctx, steps)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    evd.evd_check(sim.ctx)
+    ms = a.elapsed_time(b) / steps
+    kernel = "k_step_tma" if evd.evd_get_kernel(sim.ctx) == evd.EVD_KERNEL_TMA else "k_step"
+    sim.close()
+    peak, peak_kind = measured_peaks()
+    bpl = bytes_per_ssu(wl, prec) * wl.ns * wl.nsites
+    achieved = bpl / (ms * 1e-3) / 1e9
+    return {"precision": prec, "ms_per_step": ms, "value": wl.ns * wl.nsites / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "steps": steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "kernel": kernel,
+                         "bytes_per_launch": bpl}}
 
 
 def run_adjoint(args, torch, dev) -> None:
@@ -590,6 +669,24 @@ def run_ours(args) -> None:
         fp64 = {"ms_per_step": ms64, "value": ns * nsites / (ms64 * 1e-3) / 1e9, "unit": UNIT,
                 "steps": n64, "speedup": ms64 / (ms / args.steps)}
 
+    # the other storage and the batched sweep, measured after the headline's
+    # timed region: FP16 storage on the same workload, and the 512-tube sweep
+    # in FP32 with its FP64 batch beside it
+    extras = {}
+    if not args.no_extras and args.workload == "stratification" and prec == "fp32":
+        extras["fp16"] = measure_single(torch, dev, stream, wl, "fp16", x_dev, min(args.steps, 300), 5)
+        if fp64 is not None:
+            extras["fp16"]["speedup_over_fp64"] = fp64["ms_per_step"] / extras["fp16"]["ms_per_step"]
+        r = measure_tubes(torch, dev, stream, "fp32", min(args.steps, 300), 5, e2e=False, fp64=True)
+        extras["tubes"] = {"workload": tubes_config()["workload"], "precision": "fp32",
+                           "ms_per_step": r["ms_per_step"], "value": r["value"], "unit": UNIT,
+                           "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
+                                        "unit": "GB/s", "frac": r["frac"], "kernel": "k_step_batch",
+                                        "bytes_per_launch": r["bytes_per_launch"]},
+                           "schedule": r["schedule"], "graph_steps": 8,
+                           "fp64_ms_per_step": r["fp64"]["ms_per_step"], "speedup_over_fp64": r["fp64"]["speedup"],
+                           "config": tubes_config()}
+
     cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         cl = clocks.summary()
@@ -616,6 +713,7 @@ def run_ours(args) -> None:
         }
         if fp64 is not None:
             out["vs_fp64_gpu"] = fp64
+        out.update(extras)
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)
@@ -641,6 +739,8 @@ def main():
     ap.add_argument("--members", type=int, default=512, help="tubes workload: the first N tubes of the sweep")
     ap.add_argument("--schedule", default="", help="tubes workload: 'item_sites,ctas_per_sm' instead of autotuning")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (2 or 4)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP16-storage and batched-sweep measurements after the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

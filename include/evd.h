@@ -97,7 +97,13 @@ typedef enum { EVD_FP64 = 0, EVD_FP32 = 1, EVD_FP16_STORE = 2 } evd_precision;
 #define EVD_WALL_ZM 0x10u
 #define EVD_WALL_ZP 0x20u
 
-#define EVD_MAX_SPECIES 3
+/* Species per lattice: up to 6 for D2Q9 in the general kernel (the cross
+ * relaxation times then come from a dense solve of Eq.
+ * relation_tauij_diff_coeff at every node); up to 3 for D3Q19, for batch
+ * members, with the corrective forcing terms and for the adjoint (which use
+ * the closed forms of Sec. 4.1). */
+#define EVD_MAX_SPECIES 6
+#define EVD_MAX_SPECIES_D3Q19 3
 
 typedef struct {
     int lattice;          /* evd_lattice                                           */
@@ -122,7 +128,7 @@ typedef struct {
 #define EVD_FORCE_S_RHO 4u
 
 typedef struct {
-    int n_species;             /* 1 .. EVD_MAX_SPECIES                              */
+    int n_species;             /* 1 .. EVD_MAX_SPECIES (3 for D3Q19)                */
     const double* molar_mass;  /* [n_species], > 0, non-decreasing                  */
     const double* diffusivity; /* [n_species*n_species], symmetric Maxwell-Stefan   */
                                /* D_ij > 0 in lattice units; diagonal ignored        */
@@ -271,7 +277,8 @@ evd_status evd_set_force_field(evd_ctx* ctx, const double* k_host);
  * transposed gather (Eq. Second_order_spatial_interpolation and App. A).  States are recomputed from
  * checkpoints stored every checkpoint_every steps (0: about sqrt(nsteps));
  * memory: (nsteps / checkpoint_every + checkpoint_every + 3) population
- * buffers.  Leaves the context at t = nsteps of this run.  Synchronises. */
+ * buffers.  Leaves the context at t = nsteps of this run (FP64 forward).
+ * Synchronises. */
 evd_status evd_loss_gradient(evd_ctx* ctx, const double* x0, const double* n0, long long nsteps,
                              const double* target, int checkpoint_every, double* loss, double* dL_dD,
                              double* dL_dg);
@@ -288,8 +295,20 @@ evd_status evd_loss_gradient(evd_ctx* ctx, const double* x0, const double* n0, l
 #define EVD_ADJOINT_DUAL 1
 evd_status evd_set_adjoint_mode(evd_ctx* ctx, int mode);
 
-/* Rows per tile of the TMA-staged step: 2 (the default; two CTAs of 6 warps
- * per SM for three species) or 4 (one CTA of 12 warps per SM).  Same results;
+/* Storage of evd_loss_gradient's forward pass.  EVD_FP64 (the default): the
+ * context's own double-precision steps.  EVD_FP32: an internal float context
+ * (node-reference encoding, no mass correction) runs the forward pass and
+ * the checkpoint recomputation, reproducing each step's dithered rounding;
+ * every state the reverse sweep needs is decoded to doubles, and the reverse
+ * sweep (the transposed collision and gather) runs in FP64 as before.  The
+ * gradient is then that of the FP32 trajectory, whose distance from the FP64
+ * one the FP32 accuracy bounds.  In this mode the context itself stays at
+ * t = 0 of the run.  EVD_ERR_ARG for another precision. */
+evd_status evd_set_adjoint_forward(evd_ctx* ctx, int precision);
+
+/* Rows per tile of the TMA-staged step: 1 (four CTAs of 3 warps per SM for
+ * three species, each synchronising only the species of its row), 2 (the
+ * default; two CTAs of 6 warps) or 4 (one CTA of 12 warps).  Same results;
  * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not
  * apply. */
 evd_status evd_set_tile_rows(evd_ctx* ctx, int rows);

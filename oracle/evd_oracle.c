@@ -24,6 +24,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXS 6
 #define OR_MAXQ 19
@@ -421,53 +424,78 @@ static double W1(double s, int d)
     return -s * (1.0 - s) / 2.0;
 }
 
+static void stream_plane(or_state* st, const double* src, double* dst, int i, int a);
+
+/* The planes of species i in directions a and opp(a) scatter only into each
+ * other (a crossed wall deposits into a or opp(a) at the source node), so
+ * each such pair is one independent task; within a task the lower direction
+ * goes first, as in a plain loop over directions, so every destination
+ * receives its terms in the same order whether or not the tasks run in
+ * parallel (an OpenMP build runs them on all host cores; the sums are
+ * bitwise those of the serial build). */
 static void stream_push(or_state* st, const double* src, double* dst)
 {
     const or_config* cfg = &st->cfg;
-    const int ns = cfg->ns, Q = st->Q, Dm = st->Dm;
+    const int ns = cfg->ns, Q = st->Q;
+    const long nsites = st->nsites;
+    long task;
+    memset(dst, 0, sizeof(double) * (size_t)ns * Q * nsites);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (task = 0; task < (long)ns * Q; ++task) {
+        const int i = (int)(task / Q), a0 = (int)(task % Q);
+        const int a1 = st->opp[a0];
+        if (a1 < a0) continue;   /* streamed with its partner */
+        stream_plane(st, src, dst, i, a0);
+        if (a1 != a0) stream_plane(st, src, dst, i, a1);
+    }
+}
+
+/* Scatter of the plane of species i, direction a (see stream_push). */
+static void stream_plane(or_state* st, const double* src, double* dst, int i, int a)
+{
+    const or_config* cfg = &st->cfg;
+    const int Q = st->Q, Dm = st->Dm;
     const int nn[3] = {cfg->nx, cfg->ny, cfg->nz};
     const long nsites = st->nsites;
-    int i, a, k;
+    int k;
     long X;
-    memset(dst, 0, sizeof(double) * (size_t)ns * Q * nsites);
-    for (i = 0; i < ns; ++i)
-        for (a = 0; a < Q; ++a) {
-            double s[3];
-            for (k = 0; k < 3; ++k) s[k] = st->c[i] * st->e[a][k];
-            for (X = 0; X < nsites; ++X) {
-                const int xs[3] = {(int)(X % cfg->nx), (int)((X / cfg->nx) % cfg->ny),
-                                   (int)(X / ((long)cfg->nx * cfg->ny))};
-                const double val = src[((long)i * Q + a) * nsites + X];
-                int d[3];
-                for (d[2] = (Dm == 3 ? -1 : 0); d[2] <= (Dm == 3 ? 1 : 0); ++d[2])
-                    for (d[1] = -1; d[1] <= 1; ++d[1])
-                        for (d[0] = -1; d[0] <= 1; ++d[0]) {
-                            double wgt = 1.0;
-                            int dest[3], crossed = 0, dot = 0;
-                            for (k = 0; k < Dm; ++k) wgt *= W1(s[k], d[k]);
-                            if (wgt == 0.0) continue;
-                            for (k = 0; k < 3; ++k) {
-                                dest[k] = xs[k] + d[k];
-                                if (dest[k] < 0 || dest[k] >= nn[k]) {
-                                    const unsigned wall = (cfg->wall_mask >> (2 * k)) & 3u;
-                                    if (wall) {
-                                        crossed = 1;
-                                        dot += st->e[a][k] * d[k];
-                                    } else {
-                                        dest[k] = (dest[k] + nn[k]) % nn[k];
-                                    }
-                                }
-                            }
-                            if (!crossed) {
-                                const long Y = dest[0] + (long)cfg->nx * (dest[1] + (long)cfg->ny * dest[2]);
-                                dst[((long)i * Q + a) * nsites + Y] += wgt * val;
+    double s[3];
+    for (k = 0; k < 3; ++k) s[k] = st->c[i] * st->e[a][k];
+    for (X = 0; X < nsites; ++X) {
+        const int xs[3] = {(int)(X % cfg->nx), (int)((X / cfg->nx) % cfg->ny),
+                           (int)(X / ((long)cfg->nx * cfg->ny))};
+        const double val = src[((long)i * Q + a) * nsites + X];
+        int d[3];
+        for (d[2] = (Dm == 3 ? -1 : 0); d[2] <= (Dm == 3 ? 1 : 0); ++d[2])
+            for (d[1] = -1; d[1] <= 1; ++d[1])
+                for (d[0] = -1; d[0] <= 1; ++d[0]) {
+                    double wgt = 1.0;
+                    int dest[3], crossed = 0, dot = 0;
+                    for (k = 0; k < Dm; ++k) wgt *= W1(s[k], d[k]);
+                    if (wgt == 0.0) continue;
+                    for (k = 0; k < 3; ++k) {
+                        dest[k] = xs[k] + d[k];
+                        if (dest[k] < 0 || dest[k] >= nn[k]) {
+                            const unsigned wall = (cfg->wall_mask >> (2 * k)) & 3u;
+                            if (wall) {
+                                crossed = 1;
+                                dot += st->e[a][k] * d[k];
                             } else {
-                                const int b = (dot > 0) ? st->opp[a] : a;
-                                dst[((long)i * Q + b) * nsites + X] += wgt * val;
+                                dest[k] = (dest[k] + nn[k]) % nn[k];
                             }
                         }
-            }
-        }
+                    }
+                    if (!crossed) {
+                        const long Y = dest[0] + (long)cfg->nx * (dest[1] + (long)cfg->ny * dest[2]);
+                        dst[((long)i * Q + a) * nsites + Y] += wgt * val;
+                    } else {
+                        const int b = (dot > 0) ? st->opp[a] : a;
+                        dst[((long)i * Q + b) * nsites + X] += wgt * val;
+                    }
+                }
+    }
 }
 
 /* ------------------------------------------------------------------ state */
@@ -610,7 +638,7 @@ static int collide_all(or_state* st)
     double fn[OR_MAXS * OR_MAXQ] = {0}, fo[OR_MAXS * OR_MAXQ] = {0};
     double grad[(OR_MAXS + 1) * 3];
     const int need_grad = (st->cfg.flags & (OR_S_P | OR_S_RHO)) != 0;
-    int i, a;
+    int i, a, ok = 1;
     long X;
     if (need_grad) {
         /* densities of f_t at every node first: rho_i, then the mixture */
@@ -627,6 +655,11 @@ static int collide_all(or_state* st)
             st->rho_field[(long)ns * nsites + X] = r;
         }
     }
+    /* nodes collide independently (an OpenMP build runs them in parallel; a
+     * failing node then stops nothing else, and the step reports failure) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) private(fn, fo, grad, i, a) reduction(&& : ok)
+#endif
     for (X = 0; X < nsites; ++X) {
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) fn[i * Q + a] = st->f[((long)i * Q + a) * nsites + X];
@@ -635,12 +668,12 @@ static int collide_all(or_state* st)
         {
             double acc[3];
             node_force(st, X, acc);
-            if (!collide_node(st, fn, fo, NULL, acc, need_grad ? grad : NULL)) return 0;
+            if (!collide_node(st, fn, fo, NULL, acc, need_grad ? grad : NULL)) ok = 0;
         }
         for (i = 0; i < ns; ++i)
             for (a = 0; a < Q; ++a) st->fs[((long)i * Q + a) * nsites + X] = fo[i * Q + a];
     }
-    return 1;
+    return ok;
 }
 
 /* nsteps full steps: collide, then stream.  Returns steps done. */
@@ -682,6 +715,16 @@ int or_collide_node(const or_state* st, const double* f, double* fstar, or_diag*
 }
 
 int or_diag_size(void) { return (int)sizeof(or_diag); }
+
+/* Threads a step uses: the OpenMP team size of an OpenMP build, else 1. */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Observables of the current state f_t, per node:
  *   rho_i (Eq. zeroth_order_moment), x_i = rho_i/(n M_i) with n = sum rho_j/M_j,

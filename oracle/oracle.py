@@ -36,6 +36,10 @@ MAXS = 6
 MAXQ = 19
 
 
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_FLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (IEEE double, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -43,11 +47,26 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc"] + _FLAGS + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
+
+
+def build_omp(force: bool = False) -> str | None:
+    """The same source compiled with OpenMP (the streaming tasks and the node
+    collisions on all host cores; bitwise the serial results).  Returns None
+    where the compiler has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO_OMP)
+            and os.path.getmtime(_SO_OMP) >= os.path.getmtime(_SRC)):
+        return _SO_OMP
+    tmp = _SO_OMP + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-fopenmp"] + _FLAGS + ["-o", tmp, _SRC, "-lm"]
+    if subprocess.run(cmd, capture_output=True).returncode != 0:
+        return None
+    os.replace(tmp, _SO_OMP)
+    return _SO_OMP
 
 
 class Config(ctypes.Structure):
@@ -107,6 +126,8 @@ def _bind(path: str):
     L.or_get_f.argtypes = [ctypes.c_void_p, dp]
     L.or_time.restype = ctypes.c_long
     L.or_time.argtypes = [ctypes.c_void_p]
+    L.or_threads.restype = ctypes.c_int
+    L.or_threads.argtypes = []
     L.or_observables.restype = ctypes.c_int
     L.or_observables.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
     L.or_mass.argtypes = [ctypes.c_void_p, dp]
@@ -176,6 +197,11 @@ def swapped_library(path: str):
     finally:
         with _lock:
             _lib = old
+
+
+def threads() -> int:
+    """Threads a step of the library in use runs on (1 for the serial build)."""
+    return int(lib().or_threads())
 
 
 def source() -> str:

@@ -5,7 +5,8 @@ L = sum_i sum_y (xbar_i(y) - target_i(y))^2 after ``problem.nsteps`` steps,
 xbar the mean over x of the mole fractions, as a differentiable function of
 the Maxwell-Stefan diffusivities ``d_pairs`` (one per species pair i < j, in
 the order (0,1), (0,2), ..., (1,2), ...) and the body force ``g`` (g_x, g_y).
-The forward pass runs ``evd_loss_gradient`` (D2Q9, FP64), which returns the
+The forward pass runs ``evd_loss_gradient`` (D2Q9; its forward steps in FP64 or
+FP32, the reverse sweep in FP64), which returns the
 exact gradient of the discrete step together with the loss; the backward
 pass scales it.  Argument marshalling only: the steps and their adjoint run
 in the library's kernels.
@@ -32,6 +33,7 @@ class Problem:
     n0: np.ndarray | None = None
     checkpoint_every: int = 0
     mode: int = 0           # evd.EVD_ADJOINT_REVERSE (default) or evd.EVD_ADJOINT_DUAL
+    forward: str = "fp64"   # storage of the forward pass: "fp64" or "fp32" (reverse sweep in FP64)
 
 
 def pairs_to_matrix(ns: int, d_pairs) -> np.ndarray:
@@ -55,6 +57,7 @@ def loss_and_gradient(problem: Problem, d_pairs, g):
         n0 = None if problem.n0 is None else np.ascontiguousarray(problem.n0, dtype=np.float64)
         tgt = np.ascontiguousarray(problem.target, dtype=np.float64)
         evd.evd_set_adjoint_mode(sim.ctx, problem.mode)
+        evd.evd_set_adjoint_forward(sim.ctx, problem.forward)
         loss, dD, dg = evd.evd_loss_gradient(sim.ctx, x0, tgt, problem.nsteps, n0, problem.checkpoint_every)
     finally:
         sim.close()

@@ -67,8 +67,12 @@ struct evd_ctx {
     bool tma_ok;         // the TMA-staged step can run this configuration
     int kernel;          // EVD_KERNEL_GENERAL or EVD_KERNEL_TMA
     int tma_blocks;      // grid of the TMA step
-    int tma_ty;          // rows per tile of the TMA step (2 or 4)
+    int tma_ty;          // rows per tile of the TMA step (1, 2 or 4)
     int adj_mode = EVD_ADJOINT_REVERSE;   // how evd_loss_gradient transposes the collision
+    int adj_forward = EVD_FP64;           // storage of the adjoint's forward pass
+    unsigned wall_mask;                   // as given at creation
+    std::vector<double> sp_M, sp_D;       // the species table as given at creation
+    double sp_tau1, sp_g[3];
     int last_parts;      // mass partials written by the last measuring launch
     CUtensorMap tma[2][evd::TmaLaunch::NGROUPS];   // per population buffer, per storage group
     float* lumps;        // App. A coefficients per wall class, species, direction (TMA step)
@@ -140,7 +144,11 @@ bool validate(const evd_grid* g, const evd_species* s, std::string& msg)
         if (w == 1u || w == 2u) { msg = "a dimension must be periodic or walled at both ends"; return false; }
     }
     if (g->lattice == EVD_D2Q9 && (g->wall_mask & 0x30u)) { msg = "D2Q9 has no z walls"; return false; }
-    if (s->n_species < 1 || s->n_species > EVD_MAX_SPECIES) { msg = "n_species must be 1..3"; return false; }
+    if (s->n_species < 1 || s->n_species > EVD_MAX_SPECIES) { msg = "n_species must be 1..6"; return false; }
+    if (g->lattice == EVD_D3Q19 && s->n_species > EVD_MAX_SPECIES_D3Q19) {
+        msg = "D3Q19 takes at most 3 species";
+        return false;
+    }
     if (!s->molar_mass) { msg = "molar_mass is NULL"; return false; }
     for (int i = 0; i < s->n_species; ++i) {
         if (!(s->molar_mass[i] > 0.0) || !std::isfinite(s->molar_mass[i])) { msg = "molar masses must be > 0"; return false; }
@@ -163,6 +171,10 @@ bool validate(const evd_grid* g, const evd_species* s, std::string& msg)
     if (s->flags & ~(EVD_FORCE_S_DIFF | EVD_FORCE_S_P | EVD_FORCE_S_RHO)) { msg = "unknown species flags"; return false; }
     if (s->flags && g->lattice != EVD_D2Q9) {
         msg = "the corrective forcing terms are implemented for D2Q9";
+        return false;
+    }
+    if (s->flags && s->n_species > evd::MAXS_FAST) {
+        msg = "the corrective forcing terms take at most 3 species";
         return false;
     }
     return true;
@@ -271,6 +283,12 @@ using evd::fill_params;
 using evd::plane_stride;
 using evd::validate;
 
+// Seed of the dithered rounding of the step that makes f*_t (t >= 1).
+unsigned step_seed(long long t)
+{
+    return (unsigned)((unsigned long long)t * 2654435761ull) | 1u;
+}
+
 // Global deviation references of float storage (half storage keeps one per
 // node instead; FP64 stores populations as they are).
 void set_reference(evd_ctx* c, const double* rho_ref)
@@ -315,7 +333,7 @@ cudaError_t launch_step(evd_ctx* c, const void* fin, void* fout, int flags, cons
     c->launches += 1;
     if (tma_active(c)) {
         const int in = (fin == c->buf[0]) ? 0 : 1;
-        c->last_parts = c->tma_blocks;
+        c->last_parts = evd::TmaLaunch::parts(h, c->tma_ty);
         if (c->precision == EVD_FP32)
             return evd::launch_step_tma<1>(h, c->tma_ty, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
         return evd::launch_step_tma<2>(h, c->tma_ty, c->tma[in], fin, fout, mp, e, flags, corr, c->lumps, st);
@@ -424,11 +442,11 @@ evd_k_mass_finish(const double* __restrict__ part, int nblocks, int ns, const do
 // positive doubles (which order as unsigned integers), by atomic min / max.
 __global__ void __launch_bounds__(128)
 evd_k_field_range(const double* __restrict__ x, const double* __restrict__ nf, int nsites, int ns,
-                  double m0, double m1, double m2, unsigned long long* __restrict__ range)
+                  const evd::MassTable mt, unsigned long long* __restrict__ range)
 {
     const int node = blockIdx.x * 128 + threadIdx.x;
     const bool active = node < nsites;
-    const double M[3] = {m0, m1, m2};
+    const double* M = mt.M;
     const double n = active ? (nf ? nf[node] : 1.0) : 1.0;
     for (int i = 0; i < ns; ++i) {
         const double v = active ? x[(long long)i * nsites + node] * M[i] * n : 0.0;
@@ -447,12 +465,12 @@ evd_k_field_range(const double* __restrict__ x, const double* __restrict__ nf, i
 // Per-block partials of sum_x x_i M_i n (the initial species masses).
 __global__ void __launch_bounds__(128)
 evd_k_field_mass(const double* __restrict__ x, const double* __restrict__ nf, int nsites, int ns,
-                 double m0, double m1, double m2, double* __restrict__ part)
+                 const evd::MassTable mt, double* __restrict__ part)
 {
-    __shared__ double sm[3][4];
+    __shared__ double sm[evd::MAXS][4];
     const int node = blockIdx.x * 128 + threadIdx.x;
     const bool active = node < nsites;
-    const double M[3] = {m0, m1, m2};
+    const double* M = mt.M;
     const double n = active ? (nf ? nf[node] : 1.0) : 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = 0; i < ns; ++i) {
@@ -586,7 +604,7 @@ bool build_lumps(evd_ctx* c)
 
 bool tma_setup(evd_ctx* c)
 {
-    if (c->lattice != EVD_D3Q19 || c->precision == EVD_FP64) return false;
+    if (c->lattice != EVD_D3Q19 || c->precision == EVD_FP64 || c->ns > evd::MAXS_FAST) return false;
     if (!c->hp.wall[0] || !c->hp.wall[1]) return false;
     if (c->nx < 2 || c->ny < 2 || (c->hp.wall[2] && c->nz < 2)) return false;
     const int planes = buffer_planes(c->lattice, c->precision, c->ns);
@@ -651,6 +669,12 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
     c->stream = (cudaStream_t)stream;
     c->nblocks = (c->nsites + BLOCK - 1) / BLOCK;
     fill_params(c->hp, grid, species);
+    c->wall_mask = grid->wall_mask;
+    c->sp_M.assign(species->molar_mass, species->molar_mass + c->ns);
+    if (c->ns > 1) c->sp_D.assign(species->diffusivity, species->diffusivity + c->ns * c->ns);
+    else c->sp_D.assign(1, 0.0);
+    c->sp_tau1 = species->tau1;
+    for (int k = 0; k < 3; ++k) c->sp_g[k] = species->g[k];
     double zero[MAXS] = {0, 0, 0};
     set_reference(c, zero);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -689,7 +713,7 @@ evd_status create_common(const evd_grid* grid, const evd_species* species, void*
     c->kernel = c->tma_ok ? EVD_KERNEL_TMA : EVD_KERNEL_GENERAL;
     c->tma_blocks = c->tma_ok ? evd::TmaLaunch::grid(c->hp, c->tma_ty) : 0;
     // partials for either tile height, so that evd_set_tile_rows never reallocates
-    const int max_tma = c->tma_ok ? evd::TmaLaunch::grid(c->hp, 2) : 0;
+    const int max_tma = c->tma_ok ? evd::TmaLaunch::parts(c->hp, 1) : 0;
     const int max_parts = c->nblocks > max_tma ? c->nblocks : max_tma;
     const size_t part_bytes = ((size_t)max_parts * c->ns * sizeof(double) + 255) / 256 * 256;
     e = cudaMalloc(&c->small, part_bytes + 6 * 256);
@@ -783,8 +807,9 @@ evd_status evd_set_fields_device(evd_ctx* c, const double* x_dev, const double* 
     // initial species masses sum_x x_i M_i n in FP64: the target of the mass
     // correction and, for deviation storage, the reference densities
     c->launches += 1;
-    evd_k_field_mass<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, c->hp.M[0],
-                                                        c->hp.M[1], c->hp.M[2], c->mass_part);
+    evd::MassTable mt;
+    for (int i = 0; i < MAXS; ++i) mt.M[i] = c->hp.M[i];
+    evd_k_field_mass<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, mt, c->mass_part);
     CK(c, cudaGetLastError());
     evd_status s0 = finish_mass(c, c->m_target);
     if (s0 != EVD_OK) return s0;
@@ -793,8 +818,7 @@ evd_status evd_set_fields_device(evd_ctx* c, const double* x_dev, const double* 
         CK(c, cudaMemsetAsync(c->range, 0xff, c->ns * sizeof(unsigned long long), c->stream));
         CK(c, cudaMemsetAsync(c->range + c->ns, 0, c->ns * sizeof(unsigned long long), c->stream));
         c->launches += 1;
-        evd_k_field_range<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, c->hp.M[0], c->hp.M[1],
-                                                             c->hp.M[2], c->range);
+        evd_k_field_range<<<c->nblocks, 128, 0, c->stream>>>(x_dev, n_dev, c->nsites, c->ns, mt, c->range);
         CK(c, cudaGetLastError());
     }
     if (c->precision != EVD_FP64) {
@@ -895,6 +919,8 @@ evd_status evd_step(evd_ctx* c, long long nsteps)
         // of f_t; the deficit from the FP64 targets is re-injected uniformly
         // in the next step
         const bool measure = c->mc_every > 0 && ((c->t + 1) % c->mc_every == 0);
+        // reduced storage dithers its rounding with a fresh seed every step
+        c->hp.seed = c->precision == EVD_FP64 ? 0u : step_seed(c->t + 1);
         const int apply = c->corr_pending;
         CK(c, launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], measure ? FLAG_MASS : 0,
                           apply >= 0 ? c->corr[apply] : nullptr));
@@ -1070,10 +1096,19 @@ evd_status evd_set_adjoint_mode(evd_ctx* c, int mode)
     return EVD_OK;
 }
 
+evd_status evd_set_adjoint_forward(evd_ctx* c, int precision)
+{
+    if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
+    if (precision != EVD_FP64 && precision != EVD_FP32)
+        return fail(c, EVD_ERR_ARG, "the adjoint's forward pass runs in EVD_FP64 or EVD_FP32");
+    c->adj_forward = precision;
+    return EVD_OK;
+}
+
 evd_status evd_set_tile_rows(evd_ctx* c, int rows)
 {
     if (!c) return fail(nullptr, EVD_ERR_ARG, "ctx is NULL");
-    if (rows != 2 && rows != 4) return fail(c, EVD_ERR_ARG, "rows must be 2 or 4");
+    if (rows != 1 && rows != 2 && rows != 4) return fail(c, EVD_ERR_ARG, "rows must be 1, 2 or 4");
     if (!c->tma_ok) return fail(c, EVD_ERR_ARG, "the TMA-staged step does not apply to this configuration");
     if (rows == c->tma_ty) return EVD_OK;
     DeviceGuard dg(c->device);
@@ -1144,6 +1179,7 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
     if (!x0 || !target || !loss) return fail(c, EVD_ERR_ARG, "x0, target and loss must not be NULL");
     if (c->lattice != EVD_D2Q9 || c->precision != EVD_FP64)
         return fail(c, EVD_ERR_ARG, "the adjoint is implemented for D2Q9 with FP64 storage");
+    if (c->ns > evd::MAXS_FAST) return fail(c, EVD_ERR_ARG, "the adjoint takes at most 3 species");
     if (c->kf || c->hp.flags || c->mc_every)
         return fail(c, EVD_ERR_ARG, "the adjoint takes a uniform g, no corrective terms, no mass correction");
     if (nsteps < 1) return fail(c, EVD_ERR_ARG, "nsteps must be >= 1");
@@ -1163,6 +1199,34 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
     const int np = evd::AdjLaunch::nparams(c->ns);
     const long long ncp = (N - 1) / K + 1;          // checkpoints f*_0, f*_K, ...
     DevBufs mem;
+    // FP32 forward: an internal float context (node references, no mass
+    // correction) runs the forward pass and recomputes the segments with the
+    // same dither seeds; each state the reverse sweep needs is decoded to
+    // doubles.  The reverse sweep itself runs in FP64 either way.
+    struct Owned {
+        evd_ctx* p = nullptr;
+        ~Owned() { if (p) evd_destroy(p); }
+    } fcp;
+    const bool f32 = c->adj_forward == EVD_FP32;
+    if (f32) {
+        const evd_grid g32{c->lattice, EVD_FP32, c->nx, c->ny, c->nz, c->wall_mask};
+        evd_species s32{c->ns, c->sp_M.data(), c->sp_D.data(), c->sp_tau1, {c->sp_g[0], c->sp_g[1], c->sp_g[2]}, 0u};
+        s = create_common(&g32, &s32, c->stream, nullptr, nullptr, 0, &fcp.p);
+        if (s != EVD_OK) return fail(c, s, std::string("FP32 forward context: ") + g_create_error);
+        fcp.p->ref_mode = EVD_REF_NODE;
+        fcp.p->mc_every = 0;
+        s = evd_set_fields(fcp.p, x0, n0);
+        if (s != EVD_OK) return fail(c, s, std::string("FP32 forward: ") + fcp.p->err);
+    }
+    evd_ctx* fc = fcp.p;
+    void* dec = nullptr;   // a decoded state (FP32 forward)
+    if (f32) CK(c, mem.alloc(bb, &dec));
+    auto as_f64 = [&](const void* state) -> const double* {
+        if (!f32) return (const double*)state;
+        c->launches += 1;
+        const cudaError_t e = evd::DecodeLaunch::f32n_to_f64(fc->hp, state, (double*)dec, c->stream);
+        return e == cudaSuccess ? (const double*)dec : nullptr;
+    };
     void *f0 = nullptr, *lam_f = nullptr, *lam_s = nullptr, *xd = nullptr, *nd = nullptr, *dldx = nullptr,
          *part = nullptr, *grad = nullptr;
     CK(c, mem.alloc(bb, &f0));
@@ -1174,24 +1238,26 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
     CK(c, mem.alloc((size_t)evd::AdjLaunch::nblocks(c->hp) * np * sizeof(double), &part));
     CK(c, mem.alloc(np * sizeof(double), &grad));
     std::vector<void*> cp(ncp, nullptr), seg(K, nullptr);
-    for (auto& q : cp) CK(c, mem.alloc(bb, &q));
-    for (auto& q : seg) CK(c, mem.alloc(bb, &q));
+    const size_t sb = f32 ? fc->buf_bytes : bb;   // bytes of a stored state
+    for (auto& q : cp) CK(c, mem.alloc(sb, &q));
+    for (auto& q : seg) CK(c, mem.alloc(sb, &q));
+    evd_ctx* fw = f32 ? fc : c;   // the context that runs the forward pass
     cudaStream_t st = c->stream;
     CK(c, cudaMemcpyAsync(xd, x0, c->ns * n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (n0) CK(c, cudaMemcpyAsync(nd, n0, n * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemsetAsync(grad, 0, np * sizeof(double), st));
     // forward: f_0 and the checkpoints, then N steps to the state the loss reads
     CK(c, cudaMemcpyAsync(f0, c->buf[c->cur ^ 1], bb, cudaMemcpyDeviceToDevice, st));
-    CK(c, cudaMemcpyAsync(cp[0], c->buf[c->cur], bb, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(cp[0], fw->buf[fw->cur], sb, cudaMemcpyDeviceToDevice, st));
     for (long long t = 1; t <= N; ++t) {
-        s = evd_step(c, 1);
-        if (s != EVD_OK) return s;
-        if (t < N && t % K == 0) CK(c, cudaMemcpyAsync(cp[t / K], c->buf[c->cur], bb, cudaMemcpyDeviceToDevice, st));
+        s = evd_step(fw, 1);
+        if (s != EVD_OK) return f32 ? fail(c, s, std::string("FP32 forward: ") + fc->err) : s;
+        if (t < N && t % K == 0) CK(c, cudaMemcpyAsync(cp[t / K], fw->buf[fw->cur], sb, cudaMemcpyDeviceToDevice, st));
     }
     // the loss: row averages of the mole fractions of f_N against the target
     std::vector<double> x(c->ns * n), g(c->ns * n, 0.0);
-    s = readout_to_host(c, x.data(), nullptr, nullptr, nullptr);
-    if (s != EVD_OK) return s;
+    s = readout_to_host(fw, x.data(), nullptr, nullptr, nullptr);
+    if (s != EVD_OK) return f32 ? fail(c, s, std::string("FP32 forward: ") + fc->err) : s;
     double L = 0.0;
     for (int i = 0; i < c->ns; ++i)
         for (int y = 0; y < c->ny; ++y) {
@@ -1207,19 +1273,26 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
     // reverse sweep: lambda_N, then lambda*_{N-1} = G^T lambda_N
     const HostParams& h = c->hp;
     c->launches += 2;
-    CK(c, evd::AdjLaunch::readout(h, (const double*)c->buf[c->cur ^ 1], (const double*)dldx, (double*)lam_f, st));
+    const double* fN1 = as_f64(fw->buf[fw->cur ^ 1]);   // f*_{N-1}
+    if (!fN1) return cuda_fail(c, cudaGetLastError(), "decode");
+    CK(c, evd::AdjLaunch::readout(h, fN1, (const double*)dldx, (double*)lam_f, st));
     CK(c, evd::AdjLaunch::gather_t(h, (const double*)lam_f, (double*)lam_s, st));
     long long seg_id = -1;
     for (long long t = N - 1; t >= 1; --t) {
         // f*_{t-1}, recomputed from its checkpoint with the rest of its segment
         const long long j = (t - 1) / K;
         if (j != seg_id) {
-            CK(c, cudaMemcpyAsync(seg[0], cp[j], bb, cudaMemcpyDeviceToDevice, st));
+            CK(c, cudaMemcpyAsync(seg[0], cp[j], sb, cudaMemcpyDeviceToDevice, st));
             const long long last = std::min(j * K + K - 1, N - 2);
-            for (long long q = 1; q <= last - j * K; ++q) CK(c, launch_step(c, seg[q - 1], seg[q], 0, nullptr));
+            for (long long q = 1; q <= last - j * K; ++q) {
+                // the forward's step to f*_{jK+q}, with its dither seed
+                if (f32) fc->hp.seed = step_seed(j * K + q);
+                CK(c, launch_step(fw, seg[q - 1], seg[q], 0, nullptr));
+            }
             seg_id = j;
         }
-        const double* fprev = (const double*)seg[(t - 1) - j * K];
+        const double* fprev = as_f64(seg[(t - 1) - j * K]);
+        if (!fprev) return cuda_fail(c, cudaGetLastError(), "decode");
         c->launches += 3;
         CK(c, evd::AdjLaunch::collide(h, fprev, false, (const double*)lam_s, (double*)lam_f, (double*)part,
                                       (double*)grad, c->adj_mode == EVD_ADJOINT_DUAL, st));
@@ -1236,6 +1309,7 @@ evd_status evd_loss_gradient(evd_ctx* c, const double* x0, const double* n0, lon
     CK(c, cudaStreamSynchronize(st));
     s = evd_check(c);
     if (s != EVD_OK) return s;
+    if (f32 && (s = evd_check(fc)) != EVD_OK) return fail(c, s, std::string("FP32 forward: ") + fc->err);
     if (dL_dD) {
         for (int q = 0; q < c->ns * c->ns; ++q) dL_dD[q] = 0.0;
         int m = 0;

@@ -425,6 +425,7 @@ evd_status evd_batch_create(int lattice, int precision, const evd_member* member
         const evd_grid g{lattice, precision, mb.nx, mb.ny, mb.nz, mb.wall_mask};
         std::string msg;
         if (mb.species.flags) msg = "the corrective forcing terms are not supported in a batch";
+        else if (mb.species.n_species > evd::MAXS_FAST) msg = "batch members take at most 3 species";
         if (!msg.empty() || !evd::validate(&g, &mb.species, msg)) {
             delete b;
             return fail(nullptr, EVD_ERR_ARG, "member " + std::to_string(m) + ": " + msg);

@@ -156,6 +156,7 @@ struct Params {
     const T* kf;           // per-node specific force [3][nsites] added to g, or nullptr
     unsigned flags;        // corrective forcing terms: bit 0 S_diff, 1 S_p, 2 S_rho
     const T* rhof;         // [ns + 1][nsites] densities of f_t (species, mixture) or nullptr
+    unsigned seed;         // per-step seed of the dithered rounding of reduced storage (0: off)
 };
 
 template <typename T>
@@ -180,6 +181,7 @@ inline Params<T> to_params(const HostParams& h)
     p.kf = (const T*)h.kf;
     p.flags = h.flags;
     p.rhof = (const T*)h.rhof;
+    p.seed = h.seed;
     // directions per class: rest, axis, diagonal
     const double n1 = h.lattice == 0 ? 4.0 : 6.0, n2 = h.lattice == 0 ? 4.0 : 12.0;
     for (int i = 0; i < MAXS; ++i) {
@@ -262,6 +264,45 @@ template <> struct Codec<__half> {
     // the value a float takes once stored
     static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
+
+// ------------------------------------------------------ dithered rounding
+// A slowly varying field is rounded the same way every step, so its rounding
+// error adds up like a steady source instead of averaging out; over tens of
+// thousands of steps that frozen error, not the random part, decides the
+// reduced-precision error.  Reduced storage therefore rounds its last
+// operation with a dither: a uniform offset of up to half a unit in the last
+// place of the result's precision, drawn from a counter-based hash of (seed of
+// the step, node, species, direction), is added before rounding to nearest,
+// which makes the rounding error zero-mean and uncorrelated from step to step.
+__device__ __forceinline__ unsigned dither_hash(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Signed uniform in [-1/2, 1/2) times u, from 32 hash bits.
+__device__ __forceinline__ float dither_scale(unsigned h, float u)
+{
+    return (float)(int)h * (u * 2.3283064365386963e-10f);
+}
+
+// One unit in the last place of v in float (0 for |v| below 2^-102).
+__device__ __forceinline__ float ulp_float(float v)
+{
+    const int e = __float_as_int(v) & 0x7f800000;
+    return e > (23 << 23) ? __int_as_float(e - (23 << 23)) : 0.0f;
+}
+
+// One unit in the last place of v once stored as a half (subnormal halves: 2^-24).
+__device__ __forceinline__ float ulp_half(float v)
+{
+    const int e = __float_as_int(v) & 0x7f800000;
+    return e >= ((127 - 14) << 23) ? __int_as_float(e - (10 << 23)) : 5.9604644775390625e-8f;
+}
 
 // Plane holding the node reference densities of species i (node encodings).
 template <int LAT, int NS, typename S>
@@ -565,9 +606,11 @@ __device__ __forceinline__ void load_raw(const Params<T>& p, const S* __restrict
 // node's species densities.  Node encodings store the new reference
 // R* = rho (rounded as stored: half storage keeps it as a half) and the
 // deviations from it, g - w_a (R* - R0) (R* - R0 is exact: both are close).
-template <int LAT, int NS, typename S, typename T>
+// DITHER (half storage, p.seed != 0): the conversion to half is dithered.
+template <int LAT, int NS, typename S, bool DITHER = false, typename T>
 __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fout, int node,
-                                          const T (&f)[NS][Lat<LAT>::Q], const T (&rho)[NS], const T (&R0)[NS])
+                                          const T (&f)[NS][Lat<LAT>::Q], const T (&rho)[NS], const T (&R0)[NS],
+                                          unsigned h0 = 0)
 {
     constexpr int Q = Lat<LAT>::Q;
     static_for<0, NS>([&](auto ic) {
@@ -582,6 +625,12 @@ __device__ __forceinline__ void store_all(const Params<T>& p, S* __restrict__ fo
             constexpr int A = decltype(ac)::value;
             T v = f[I][A];
             if constexpr (Codec<S>::NODE) v -= p.wl[wclass<LAT>(A)] * dR;
+            if constexpr (DITHER && std::is_same<S, __half>::value) {
+                if (p.seed) {
+                    const unsigned r = dither_hash(h0 ^ ((unsigned)(I * 32 + A) * 0x9E3779B1u));
+                    v += dither_scale(r, ulp_half((float)v));
+                }
+            }
             Codec<S>::st(fout + (long long)plane_of<LAT, NS>(I, A) * p.pstride + node, v);
         });
     });
@@ -635,6 +684,66 @@ struct NodeState {
     T rho_mix, n;
 };
 
+// Cross relaxation rates X_ij = 1/tau_ij of N > 3 species, the system of
+// Eq. (relation_tauij_diff_coeff) that the paper solves iteratively in a
+// multicomponent mixture: one equation per pair i < j (species ordered by
+// molar mass),
+//   A_ij X_ij + (1/D_ij) sum_{s != i,j} rho_s X_sj = B_ij,
+//   A_ij = (rho_i + rho_j)/D_ij + 2 n^2 M_i M_j/(p dt),  B_ij = 2 rho/(D_ij dt),
+// solved directly by Gaussian elimination with partial pivoting (NP = N(N-1)/2
+// unknowns, the pairs in the order (0,1), (0,2), ..., (1,2), ...).  For N = 2
+// and 3 the same system has the closed forms used above.
+template <int NS, typename T>
+__device__ __forceinline__ int pair_slot(int a, int b)
+{
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo * NS - lo * (lo + 1) / 2 + (hi - lo - 1);
+}
+
+template <int NS, typename T>
+__device__ void tau_dense(const Params<T>& p, const T (&rho)[NS], T rho_mix, T n, T (&X)[MAXS][MAXS],
+                          unsigned& err)
+{
+    constexpr int NP = NS * (NS - 1) / 2;
+    T A[NP][NP + 1];
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+#pragma unroll
+        for (int c = 0; c <= NP; ++c) A[r][c] = (T)0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NS; ++j) {
+            const int r = pair_slot<NS, T>(i, j);
+            A[r][r] += (rho[i] + rho[j]) * p.iD[i][j] + n * p.MM[i][j];   // MM = 2 n M_i M_j/(p dt) / n
+#pragma unroll
+            for (int q = 0; q < NS; ++q)
+                if (q != i && q != j) A[r][pair_slot<NS, T>(q, j)] += rho[q] * p.iD[i][j];
+            A[r][NP] = (T)2 * rho_mix * p.iD[i][j];
+        }
+    for (int c = 0; c < NP; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < NP; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (!(A[piv][c] != (T)0)) { err |= ERR_TAU; return; }
+        if (piv != c)
+            for (int k = 0; k <= NP; ++k) { const T t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        for (int r = c + 1; r < NP; ++r) {
+            const T m = A[r][c] / A[c][c];
+            for (int k = c; k <= NP; ++k) A[r][k] -= m * A[c][k];
+        }
+    }
+    for (int c = NP - 1; c >= 0; --c) {
+        T acc = A[c][NP];
+        for (int k = c + 1; k < NP; ++k) acc -= A[c][k] * A[k][NP];
+        A[c][NP] = acc / A[c][c];
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NS; ++j) X[i][j] = X[j][i] = A[pair_slot<NS, T>(i, j)][NP];
+}
+
 // Moments (Eq. zeroth_order_moment, first_order_moment_force with F_i =
 // rho_i g, Eq. Sirovich_mixture_density and _velocity), n = sum rho_i/M_i and
 // the cross relaxation rates 1/tau_ij of Eq. (relation_tauij_diff_coeff):
@@ -643,10 +752,14 @@ struct NodeState {
 // DA: f holds deviations g = f - w R0 (deviation storage): rho_i = R0_i +
 // sum g, j_i = sum e g (the references cancel in j); R0 is the per-species
 // reference or the node's own (node_base).
-template <int LAT, int NS, bool DA = false, typename T>
+// DITHER (node references in float, p.seed != 0): rho_i = R0_i + sum g is
+// rounded with a dither (h0: the node's hash of the step seed).  The node's
+// density is stored as this float, and a change below half a unit in its
+// last place would otherwise be lost at the same node every step.
+template <int LAT, int NS, bool DA = false, bool DITHER = false, typename T>
 __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat<LAT>::Q],
                                         NodeState<NS, T>& s, unsigned& err, const T (&g)[3],
-                                        const T* R0 = nullptr)
+                                        const T* R0 = nullptr, unsigned h0 = 0)
 {
     constexpr int Q = Lat<LAT>::Q;
     s.rho_mix = (T)0;
@@ -666,6 +779,9 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
             if constexpr (ev<LAT>(A, 2) == -1) j[2] -= v;
         });
         s.drho[I] = r;
+        if constexpr (DA && DITHER) {
+            if (p.seed) r += (T)dither_scale(dither_hash(h0 ^ (0x5bd1e995u * (unsigned)(I + 1))), ulp_float((float)R0[I]));
+        }
         if constexpr (DA) r = R0[I] + r;
         if (!(r > (T)0)) err |= ERR_RHO;
         const T rinv = (T)1 / r;
@@ -705,6 +821,9 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
         X[0][1] = X[1][0] = X12;
         X[0][2] = X[2][0] = X13;
         X[1][2] = X[2][1] = X23;
+    }
+    else if constexpr (NS > 3) {
+        tau_dense<NS>(p, s.rho, s.rho_mix, s.n, X, err);
     }
     // tau_ij < 1/2 is a legitimate outcome of the relation (it happens for
     // trace species); only a non-positive or non-finite tau_ij is an error.
@@ -747,12 +866,29 @@ __device__ __forceinline__ void moments(const Params<T>& p, const T (&f)[NS][Lat
 //   S_p    = w [(e e - cs2 I)/cs2^2 . u] . grad(rho_i cs2)      (subtracted),
 //   S_rho  = w [(e e - cs2 I)/cs2 . u_i^eq] . (w_i grad rho),   w_i = rho_i/rho;
 // grad: [NS + 1][3] lattice gradients of rho_i and rho at this node.
-template <int LAT, int NS, bool DA = false, bool CORR = false, bool NODE = false, typename T>
+// shift (DA, node references): per species, the new reference minus the old
+// one; the update then yields the deviation from the new reference in its
+// one final rounding.  DITHER (float storage, p.seed != 0): that rounding is
+// dithered (h0: the node's hash of the step seed).
+template <int LAT, int NS, bool DA = false, bool CORR = false, bool NODE = false, bool DITHER = false, typename T>
 __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>::Q],
                                         const NodeState<NS, T>& s, const T (&g)[3],
-                                        const T (*grad)[3] = nullptr)
+                                        const T (*grad)[3] = nullptr, const T* shift = nullptr,
+                                        unsigned h0 = 0)
 {
     constexpr int Q = Lat<LAT>::Q;
+    // f <- f + X (deviation arithmetic): minus the reference shift, plus the
+    // dither, in the single rounding of the last addition
+    auto upd = [&](int i, int a, int c, T X) -> T {
+        if (shift) X -= p.wl[c] * shift[i];
+        if constexpr (DITHER) {
+            if (p.seed) {
+                const unsigned r = dither_hash(h0 ^ ((unsigned)(i * 32 + a) * 0x9E3779B1u));
+                X += (T)dither_scale(r, ulp_float((float)(f[i][a] + X)));
+            }
+        }
+        return f[i][a] + X;
+    };
     T Xc[NS][3], Yc[NS][3];   // the vectors the corrective terms contract with
     if constexpr (CORR) {
 #pragma unroll
@@ -815,7 +951,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
                 const T phi = fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T b = fma(p.c_inv_cs2[i], ea, Bm[i]);
                 const T B = p.tau_inv[i] + b;
-                f[i][A] += fma(p.tau_inv[i], dt[i][C] - f[i][A], fma(wr[i][C], fma(phi, B, b), S));
+                f[i][A] = upd(i, A, C, fma(p.tau_inv[i], dt[i][C] - f[i][A], fma(wr[i][C], fma(phi, B, b), S)));
             } else {
                 const T feq = wr[i][C] * fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
                 const T B = fma(p.c_inv_cs2[i], ea, Bc[i]);
@@ -859,8 +995,8 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
                     const T tB = p.tau_inv[i] + Bm[i];
                     const T E = fma(wr[i][C], fma(phiE, tB, fma(t1, bO, Bm[i])), SE);
                     const T O = fma(wr[i][C], fma(t1, tB, fma(phiE, bO, bO)), SO);
-                    f[i][A] += fma(p.tau_inv[i], dt[i][C] - f[i][A], E + O);
-                    f[i][AB] += fma(p.tau_inv[i], dt[i][C] - f[i][AB], E - O);
+                    f[i][A] = upd(i, A, C, fma(p.tau_inv[i], dt[i][C] - f[i][A], E + O));
+                    f[i][AB] = upd(i, AB, C, fma(p.tau_inv[i], dt[i][C] - f[i][AB], E - O));
                 } else {              // B = b_O + Bc
                     const T E = fma(wr[i][C], fma(phiE, Bc[i], t1 * bO), SE);
                     const T O = fma(wr[i][C], fma(t1, Bc[i], phiE * bO), SO);
@@ -924,30 +1060,54 @@ __device__ __forceinline__ void add_correction(const Params<T>& p, const double*
     });
 }
 
+// The whole step at one node (gather, correction, moments, collision, store);
+// s receives the node's moments (its densities feed the mass partials).
+template <int LAT, int NS, typename S, typename T>
+__device__ __forceinline__ void step_node(const Params<T>& p, const S* __restrict__ fin, S* __restrict__ fout,
+                                          int node, const double* __restrict__ corr, NodeState<NS, T>& s,
+                                          unsigned& err)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    constexpr bool DA = dev_arith<S>();
+    T f[NS][Q];
+    T gn[3];   // specific body force at this node
+    node_force(p, node, gn);
+    const Nbr nb = neighbours(p, node);
+    T R0[NS];
+    node_base<LAT, NS>(p, fin, node, R0);
+    gather_all<LAT, NS>(p, fin, node, nb, R0, f);
+    if (corr) add_correction<LAT, NS>(p, corr, f, R0);
+    constexpr bool FLT = !std::is_same<S, double>::value && !std::is_same<S, __half>::value;
+    constexpr bool HLF = std::is_same<S, __half>::value;
+    const unsigned h0 = dither_hash(p.seed ^ ((unsigned)node * 0x85EBCA77u));
+    moments<LAT, NS, DA, Codec<S>::NODE && FLT>(p, f, s, err, gn, R0, h0);
+    if constexpr (Codec<S>::NODE && FLT) {
+        // node references: the collision yields the deviation from the new
+        // reference rho_i (the shift from the old one folded into its last
+        // rounding), which store_all then keeps as is
+        T Rn[NS], sh[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) { Rn[i] = (T)Codec<S>::rt((float)s.rho[i]); sh[i] = Rn[i] - R0[i]; }
+        collide<LAT, NS, DA, false, true, true>(p, f, s, gn, (const T(*)[3])nullptr, sh, h0);
+        store_all<LAT, NS, S>(p, fout, node, f, s.rho, Rn);
+    } else {
+        collide<LAT, NS, DA, false, Codec<S>::NODE, FLT>(p, f, s, gn, (const T(*)[3])nullptr, (const T*)nullptr, h0);
+        store_all<LAT, NS, S, HLF>(p, fout, node, f, s.rho, R0, h0);
+    }
+}
+
 template <int LAT, int NS, typename S, typename T>
 __global__ void __launch_bounds__(BLOCK)
 k_step(const Params<T> p, const S* __restrict__ fin, S* __restrict__ fout,
        double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
        const double* __restrict__ corr)
 {
-    constexpr int Q = Lat<LAT>::Q;
-    constexpr bool DA = dev_arith<S>();
     const int node = blockIdx.x * BLOCK + threadIdx.x;
     const bool active = node < p.nsites;
-    T f[NS][Q];
-    T gn[3] = {p.g[0], p.g[1], p.g[2]};   // specific body force at this node
-    if (active) node_force(p, node, gn);
     NodeState<NS, T> s;
     unsigned err = 0;
     if (active) {
-        const Nbr nb = neighbours(p, node);
-        T R0[NS];
-        node_base<LAT, NS>(p, fin, node, R0);
-        gather_all<LAT, NS>(p, fin, node, nb, R0, f);
-        if (corr) add_correction<LAT, NS>(p, corr, f, R0);
-        moments<LAT, NS, DA>(p, f, s, err, gn, R0);
-        collide<LAT, NS, DA, false, Codec<S>::NODE>(p, f, s, gn);
-        store_all<LAT, NS>(p, fout, node, f, s.rho, R0);
+        step_node<LAT, NS>(p, fin, fout, node, corr, s, err);
         if (err) atomicOr(err_flag, err);
     }
     if (flags & F_MASS) block_mass<NS>(s.rho, active, mass_part);
@@ -1093,6 +1253,26 @@ k_readout(const Params<T> p, const S* __restrict__ fin, int flags, double* __res
         if (err) atomicOr(err_flag, err);
     }
     block_mass<NS>(s.rho, active, mass_part);
+}
+
+// Decode of a node-reference float buffer into full-size doubles (layout as
+// double storage, the same plane stride).
+template <int LAT, int NS>
+__global__ void __launch_bounds__(BLOCK)
+k_decode_f32n(const Params<float> p, const f32n* __restrict__ fin, double* __restrict__ fout)
+{
+    constexpr int Q = Lat<LAT>::Q;
+    const int node = blockIdx.x * BLOCK + threadIdx.x;
+    if (node >= p.nsites) return;
+    float R0[NS], f[NS][Q];
+    node_base<LAT, NS>(p, fin, node, R0);
+    load_raw<LAT, NS>(p, fin, node, f);
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            fout[(long long)plane_of<LAT, NS>(i, a) * p.pstride + node] =
+                (double)p.wl[wclass<LAT>(a)] * (double)R0[i] + (double)f[i][a];
 }
 
 // Full-size populations of a node (the initial state) into the arithmetic of

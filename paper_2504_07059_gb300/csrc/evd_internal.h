@@ -15,7 +15,14 @@ namespace evd {
 void set_thread_error(const std::string& msg);
 const char* thread_error();
 
-constexpr int MAXS = 3;
+constexpr int MAXS = 6;        // species of the general kernel (D2Q9)
+constexpr int MAXS_FAST = 3;   // species of the TMA step, the batch, D3Q19, the
+                               // corrective terms and the adjoint
+
+// Molar masses passed by value to the field kernels.
+struct MassTable {
+    double M[MAXS];
+};
 
 // Per-run constants in double; each precision casts them to its own type.
 struct HostParams {
@@ -36,6 +43,7 @@ struct HostParams {
     unsigned flags;          // corrective forcing terms (EVD_FORCE_S_DIFF / _S_P / _S_RHO)
     const void* rhof;        // device [ns + 1][nsites] densities of f_t for the gradient terms
     int wait_polls;          // polls of a TMA-step wait for a tile copy before it gives up
+    unsigned seed;           // per-step seed of the dithered rounding (0: off)
 };
 
 // Default of HostParams::wait_polls: far longer than any tile copy takes.
@@ -126,6 +134,15 @@ struct AdjLaunch {
                               double* part, double* grad, cudaStream_t st);
 };
 
+// Post-collision populations of a float node-reference buffer (D2Q9) as
+// doubles in the double-precision plane layout (same plane stride): f_a =
+// w_a rho + g_a, the rest f_0 = w_0 rho - sum of the others' g (the adjoint's
+// FP32-forward mode reads its states this way).  h: the float context's
+// constants.
+struct DecodeLaunch {
+    static cudaError_t f32n_to_f64(const HostParams& h, const void* fin, double* fout, cudaStream_t st);
+};
+
 inline int grid_blocks(const HostParams& h, int block) { return (h.nsites + block - 1) / block; }
 
 // The D3Q19 step with TMA-staged tiles (float and half storage only).
@@ -140,6 +157,8 @@ struct TmaLaunch {
         const int ntx = (h.nx + TX - 1) / TX, nty = (h.ny + ty - 1) / ty, zc = zchunk(h);
         return ntx * nty * ((h.nz + zc - 1) / zc);
     }
+    // mass partials of a step at tile height ty
+    static int parts(const HostParams& h, int ty) { return grid(h, ty); }
 };
 
 // lumps: App. A coefficients [27 wall classes][ns][19] x (L_self, L_opp,

@@ -1,5 +1,6 @@
 // evd_launch.cuh -- (lattice, species count) dispatch of the kernel templates
-// for one storage type S and arithmetic type T.
+// for one storage type S and arithmetic type T: 1 to 3 species on both
+// lattices, 4 to 6 on D2Q9.
 #pragma once
 
 #include "evd_device.cuh"
@@ -12,6 +13,15 @@ namespace evd {
         case 1: KERNEL<LAT, 1, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
         case 2: KERNEL<LAT, 2, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
         case 3: KERNEL<LAT, 3, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break;    \
+        case 4: if constexpr (LAT == 0) {                                            \
+                    KERNEL<LAT, 4, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break; \
+                } return cudaErrorInvalidValue;                                      \
+        case 5: if constexpr (LAT == 0) {                                            \
+                    KERNEL<LAT, 5, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break; \
+                } return cudaErrorInvalidValue;                                      \
+        case 6: if constexpr (LAT == 0) {                                            \
+                    KERNEL<LAT, 6, S, T><<<grid, BLOCK, 0, st>>>(__VA_ARGS__); break; \
+                } return cudaErrorInvalidValue;                                      \
         default: return cudaErrorInvalidValue;                                       \
     }
 

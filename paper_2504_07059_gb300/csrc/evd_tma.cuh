@@ -91,11 +91,10 @@ struct TmaLayout {
     }
     static constexpr int ring_bytes = SLOTS * slot_bytes;
     static constexpr int exch_bytes = 2 * NS * TY * TTX * 16;   // two float4 buffers
-    // float storage: wall populations of the node land here by cp.async
-    // ([direction][thread] words) instead of in registers
-    static constexpr bool CEN_SMEM = sizeof(S) == 4;
+    // App. A terms of wall nodes, [2][direction][thread] floats: written
+    // while the node's slab is resident, added one iteration later
     static constexpr int cen_offset = ring_bytes + exch_bytes;
-    static constexpr int cen_bytes = CEN_SMEM ? 19 * threads * 4 : 0;
+    static constexpr int cen_bytes = 2 * 19 * threads * 4;
     static constexpr int msum_offset = cen_offset + cen_bytes;
     static constexpr int bar_offset = msum_offset + NS * TY * 8 + 8;
     static constexpr int total_bytes = bar_offset + SLOTS * 8 + 128;   // + alignment slack
@@ -272,6 +271,20 @@ __device__ __forceinline__ float2 inplane2(const unsigned char* slot, int sp, in
     else return v;
 }
 
+// The stored value of direction A at the thread's own node in this stage's
+// tile (the centre of its stencil; half storage: not decoded).
+template <int A, int NS, typename S, int TY, int SLOTS>
+__device__ __forceinline__ float tile_center(const unsigned char* slot, int sp, int tx, int ty)
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    constexpr int g = grp<1>(A);
+    constexpr int cls = grp_cls(g);
+    constexpr int W = G::bw(cls);
+    const S* s = reinterpret_cast<const S*>(slot + G::group_offset(g)) +
+                 (sp * grp_size(g) + grp_pos<1>(A)) * G::plane_elems(g);
+    return (float)s[(ty + ((cls & 2) ? 1 : 0)) * W + tx + ((cls & 1) ? G::XP : 0)];
+}
+
 // Unit lattice speed: weights (1, 0, 0), each member's upstream node (half
 // storage: dI is that node's density rho~); a node beyond a wall reads zero.
 template <int A, int NS, typename S, int TY, int SLOTS>
@@ -298,7 +311,7 @@ __device__ __forceinline__ float edot3(const float (&v)[3])
 }
 
 template <int NS, typename S, int TY, int SLOTS>
-__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 2 ? 2 : 1)
+__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 1 ? 4 : (TY == 2 ? 2 : 1))
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
            const double* __restrict__ corr, const float4* __restrict__ lumps, int ntx, int nty, int zchunk,
@@ -313,7 +326,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     double* msum = reinterpret_cast<double*>(smem + G::msum_offset);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + G::bar_offset);
     const unsigned ring = smem_u32(smem);
-    const unsigned cen_s = smem_u32(smem + G::cen_offset);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -369,10 +381,10 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
     const bool xlo = p.wall[0] && x == 0, xhi = p.wall[0] && x == p.nx - 1;
     const bool ylo = p.wall[1] && y == 0, yhi = p.wall[1] && y == p.ny - 1;
     const bool col_wall = xlo || xhi || ylo || yhi;
+    const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
     const bool unit = p.unit[sp] != 0;   // the same for the whole warp
     const int nxy = p.nx * p.ny;
     const int pstride = (int)p.pstride;   // the host guarantees planes * pstride < 2^31
-    const int wcls_xy = (xlo ? 1 : (xhi ? 2 : 0)) + 3 * (ylo ? 1 : (yhi ? 2 : 0));
     const bool want_mass = (flags & F_MASS) != 0;
 
     // running sums, per pair k: z-moving pairs (A: node at z = k-1, B: node
@@ -401,48 +413,43 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
         const int node = x + p.nx * y + nxy * zo;
         const bool wall_node = emit && active && (col_wall || zlo || zhi);
-        float cen[Q], cenr = 0.0f;
-        if (wall_node) {
-            // the node's own post-collision populations, for the App. A terms:
-            // float storage copies them to shared memory without holding
-            // registers (waited for just before the lumps), half storage
-            // loads them into registers
-            static_for<1, Q>([&](auto ac) {
-                constexpr int A = decltype(ac)::value;
-                if constexpr (G::CEN_SMEM)
-                    cp_async4(cen_s + (unsigned)((A * G::threads + threadIdx.x) * 4),
-                              fin + (plane_of<1, NS>(sp, A) * pstride + node));
-                else
-                    cen[A] = (float)fin[plane_of<1, NS>(sp, A) * pstride + node];
-            });
-            if constexpr (G::LOCAL) cenr = (float)fin[ref_plane<1, NS>(sp) * pstride + node];
-        }
+        // the node of this stage's slab, finished next iteration, at a wall
+        const bool wall_next = !halo && active && (col_wall || (zwall && (k == 0 || k == p.nz - 1)));
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1), wait_polls);
-        // float storage: the App. A terms of a wall node, from its own
-        // populations (copied to shared memory at the top of the iteration),
-        // replace them there now, while few registers are live; they join the
-        // gathered values once those are formed
-        const float4* L = lumps + ((wcls_xy + 9 * (zlo ? 1 : (zhi ? 2 : 0))) * NS + sp) * Q;
-        if constexpr (G::CEN_SMEM) {
-            if (wall_node) {
-                cp_async_wait_all();
-                float* cw = reinterpret_cast<float*>(smem + G::cen_offset) + threadIdx.x;
-                static_for<0, NP>([&](auto kc) {
-                    constexpr int K = decltype(kc)::value;
-                    constexpr int A = 2 * K + 1, B = A + 1;
-                    const float ref = p.ref[sp][wclass<1>(A)];
-                    const float4 la = __ldg(L + A), lb = __ldg(L + B);
-                    const float ca = cw[A * G::threads], cb = cw[B * G::threads];
-                    cw[A * G::threads] = la.x * ca + la.y * cb + ref * la.z;
-                    cw[B * G::threads] = lb.x * cb + lb.y * ca + ref * lb.z;
-                });
-            }
-        }
         // half storage: this stage's node densities around the node (the
         // density term of every stencil is taken from them once per stage)
         float rd[3][3] = {};
         if constexpr (G::LOCAL)
             if (ok) dens_block<NS, S, TY, SLOTS>(base, sp, tx, ty, rd);
+        // App. A terms of the wall node of this slab, from its own
+        // post-collision populations, which are in this stage's tile (the
+        // centre of every plane): L_self f*_a + L_opp f*_abar (+ the reference
+        // the weights carry, float storage).  Computed now, while few
+        // registers are live, into this iteration's half of the term buffer;
+        // they join the node's gathered values next iteration.
+        if (ok && wall_next) {
+            const int zc_next = zwall ? (k == 0 ? 1 : (k == p.nz - 1 ? 2 : 0)) : 0;   // z wall class
+            const float4* L = lumps + ((wcls_xy + 9 * zc_next) * NS + sp) * Q;
+            float* cw = reinterpret_cast<float*>(smem + G::cen_offset) + (idx & 1) * Q * G::threads + threadIdx.x;
+            static_for<0, NP>([&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                constexpr int A = 2 * K + 1, B = A + 1;
+                const float4 la = __ldg(L + A), lb = __ldg(L + B);
+                float ca = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
+                float cb = tile_center<B, NS, S, TY, SLOTS>(base, sp, tx, ty);
+                if constexpr (G::LOCAL) {   // decoded with the node's density
+                    const float wa = p.wl[wclass<1>(A)];
+                    ca = fmaf(wa, rd[1][1], ca);
+                    cb = fmaf(wa, rd[1][1], cb);
+                    cw[A * G::threads] = la.x * ca + la.y * cb;
+                    cw[B * G::threads] = lb.x * cb + lb.y * ca;
+                } else {   // deviations, plus the reference the weights carry
+                    const float ref = p.ref[sp][wclass<1>(A)];
+                    cw[A * G::threads] = la.x * ca + la.y * cb + ref * la.z;
+                    cw[B * G::threads] = lb.x * cb + lb.y * ca + ref * lb.z;
+                }
+            });
+        }
         float f0;
         float2 F[NP];
         if (ok && unit) {
@@ -508,25 +515,14 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         // ---- node (x, y, zo): wall terms, correction, moments
         float rho = 1.0f, drho = 0.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
         if (ok && emit) {
-            if (wall_node) {
-                if constexpr (G::CEN_SMEM) {
-                    const float* cs = reinterpret_cast<const float*>(smem + G::cen_offset) + threadIdx.x;
-                    static_for<0, NP>([&](auto kc) {
-                        constexpr int K = decltype(kc)::value;
-                        constexpr int A = 2 * K + 1;
-                        F[K] = padd(F[K], make_float2(cs[A * G::threads], cs[(A + 1) * G::threads]));
-                    });
-                } else {   // half storage: own populations in registers, decoded with their node density
-                    static_for<0, NP>([&](auto kc) {
-                        constexpr int K = decltype(kc)::value;
-                        constexpr int A = 2 * K + 1, B = A + 1;
-                        const float wa = p.wl[wclass<1>(A)];
-                        const float4 la = __ldg(L + A), lb = __ldg(L + B);
-                        const float ca = fmaf(wa, cenr, cen[A]), cb = fmaf(wa, cenr, cen[B]);
-                        F[K].x += la.x * ca + la.y * cb;
-                        F[K].y += lb.x * cb + lb.y * ca;
-                    });
-                }
+            if (wall_node) {   // the App. A terms computed last iteration
+                const float* cs =
+                    reinterpret_cast<const float*>(smem + G::cen_offset) + ((idx - 1) & 1) * Q * G::threads + threadIdx.x;
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    constexpr int A = 2 * K + 1;
+                    F[K] = padd(F[K], make_float2(cs[A * G::threads], cs[(A + 1) * G::threads]));
+                });
             }
             // moments from the pairs: s = f_A + f_B adds to rho, d = f_A - f_B
             // to the momentum along A's components (sums start from a term)
@@ -715,7 +711,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         // s % SLOTS, so each is waited for with that phase's parity (a stage
         // that already landed returns at once).  These waits always take the
         // full poll count.
-        cp_async_wait_all();   // this thread's wall-population copies
         if (threadIdx.x == 0) {
             atomicOr(err_flag, ERR_TIMEOUT);
             const int last = min(fail_idx + SLOTS - 1, nstage - 1);

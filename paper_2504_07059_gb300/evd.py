@@ -21,7 +21,8 @@ EVD_OK, EVD_ERR_ARG, EVD_ERR_CUDA, EVD_ERR_UNSTABLE, EVD_ERR_TIMEOUT, EVD_ERR_ST
 EVD_D2Q9, EVD_D3Q19 = 0, 1
 EVD_FP64, EVD_FP32, EVD_FP16_STORE = 0, 1, 2
 EVD_WALL_XM, EVD_WALL_XP, EVD_WALL_YM, EVD_WALL_YP, EVD_WALL_ZM, EVD_WALL_ZP = (1, 2, 4, 8, 16, 32)
-EVD_MAX_SPECIES = 3
+EVD_MAX_SPECIES = 6
+EVD_MAX_SPECIES_D3Q19 = 3
 EVD_KERNEL_AUTO, EVD_KERNEL_GENERAL, EVD_KERNEL_TMA = 0, 1, 2
 EVD_ADJOINT_REVERSE, EVD_ADJOINT_DUAL = 0, 1
 EVD_FORCE_S_DIFF, EVD_FORCE_S_P, EVD_FORCE_S_RHO = 1, 2, 4
@@ -87,6 +88,7 @@ _SIGNATURES = {
     "evd_get_kernel": (ctypes.c_int, [_vp]),
     "evd_set_tile_rows": (_st, [_vp, ctypes.c_int]),
     "evd_set_adjoint_mode": (_st, [_vp, ctypes.c_int]),
+    "evd_set_adjoint_forward": (_st, [_vp, ctypes.c_int]),
     "evd_set_force_field": (_st, [_vp, _vp]),
     "evd_loss_gradient": (_st, [_vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "evd_set_mass_correction": (_st, [_vp, ctypes.c_int]),
@@ -316,6 +318,12 @@ def evd_loss_gradient(ctx, x0, target, nsteps: int, n0=None, checkpoint_every: i
 
 def evd_set_adjoint_mode(ctx, mode: int):
     _check(lib().evd_set_adjoint_mode(ctx, int(mode)), ctx)
+
+
+def evd_set_adjoint_forward(ctx, precision):
+    """precision: "fp64" / "fp32" or EVD_FP64 / EVD_FP32."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().evd_set_adjoint_forward(ctx, p), ctx)
 
 
 def evd_set_tile_rows(ctx, rows: int):

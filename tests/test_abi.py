@@ -43,8 +43,8 @@ def test_version_and_required_bytes(evd):
 @pytest.mark.parametrize("bad", [
     dict(lattice=7), dict(precision=9), dict(nz=2), dict(nx=0), dict(wall_mask=0b000100),
     dict(M=[2.0, 1.0]), dict(M=[1.0, -2.0]), dict(tau1=0.5), dict(D=[[0, 0.05], [0.07, 0]]),
-    dict(D=[[0, -1.0], [-1.0, 0]]), dict(g=(0, 0, 1e-6)), dict(M=[1.0, 2.0, 3.0, 4.0]),
-    dict(wall_mask=0b010000)])
+    dict(D=[[0, -1.0], [-1.0, 0]]), dict(g=(0, 0, 1e-6)), dict(M=[1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0]),
+    dict(lattice=1, nz=2, M=[1.0, 2.0, 3.0, 4.0]), dict(wall_mask=0b010000)])
 def test_invalid_configurations_are_rejected_before_any_cuda_call(evd, bad):
     M = bad.get("M", [1.0, 2.0])
     ns = len(M)
@@ -107,3 +107,18 @@ def test_corrective_forcing_flags_are_checked(evd):
                                                                            flags=evd.EVD_FORCE_S_DIFF).struct))
     with pytest.raises(evd.EVDError):
         evd.evd_batch_create(evd.EVD_D2Q9, evd.EVD_FP64, arr)
+
+
+def test_species_limits_per_lattice(evd):
+    """Up to six species on D2Q9 (dense solve of the tau_ij system), three on
+    D3Q19; the corrective terms take three at most."""
+    for ns in range(1, 7):
+        M = [1.0 + k for k in range(ns)]
+        sp = evd.SpeciesTable(M, np.full((ns, ns), 0.05), 1.0)
+        g2 = evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP64, (6, 8), 0)
+        assert evd.evd_required_bytes(g2, sp) == 64 * ns * 9 * 8
+        g3 = evd.make_grid(evd.EVD_D3Q19, evd.EVD_FP32, (4, 4, 4), 0)
+        assert (evd.evd_required_bytes(g3, sp) > 0) == (ns <= 3)
+    M = [1.0, 2.0, 3.0, 4.0]
+    sp = evd.SpeciesTable(M, np.full((4, 4), 0.05), 1.0, flags=evd.EVD_FORCE_S_DIFF)
+    assert evd.evd_required_bytes(evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP64, (6, 8), 0), sp) == 0

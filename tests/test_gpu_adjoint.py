@@ -151,3 +151,89 @@ def test_adjoint_rejects_what_it_does_not_cover(evd):
         evd.evd_set_adjoint_mode(sim.ctx, 7)
     assert ei.value.status == evd.EVD_ERR_ARG
     sim.close()
+
+
+# ---------------------------------------------------------------- the inverse problem at full size
+def gpu_loss(prob: ADJ.Problem, d_pairs, g, precision="fp64"):
+    """The loss from the library's forward step alone (no adjoint code): FP64
+    (or FP32) steps, mole fractions read back, L summed here."""
+    from paper_2504_07059_gb300 import evd
+    ns = len(prob.molar_mass)
+    sim = evd.Simulation(evd.EVD_D2Q9, prob.shape, prob.wall_mask, prob.molar_mass,
+                         ADJ.pairs_to_matrix(ns, d_pairs), prob.tau1, (float(g[0]), float(g[1])), precision)
+    try:
+        sim.set_fields(prob.x0, prob.n0)
+        sim.step(prob.nsteps)
+        xbar = sim.mole_fractions()[:, 0].mean(axis=2)
+    finally:
+        sim.close()
+    return float(((xbar - prob.target) ** 2).sum())
+
+
+def inverse_problem(steps):
+    """The 128 x 512 ternary tube with gravity (M = 2/28/44); the target is
+    the FP64 run with every diffusivity x 1.1 and the force x 0.9."""
+    wl = W.loschmidt_ternary_gravity(nx=128, ny=512)
+    d = [wl.D[0, 1], wl.D[0, 2], wl.D[1, 2]]
+    g = (0.0, wl.g[1])
+    prob = ADJ.Problem(wl.shape[:2], wl.wall_mask, wl.M, wl.tau1, wl.x, np.zeros((3, 512)), steps)
+    from paper_2504_07059_gb300 import evd
+    sim = evd.Simulation(evd.EVD_D2Q9, prob.shape, prob.wall_mask, prob.molar_mass,
+                         ADJ.pairs_to_matrix(3, 1.1 * np.asarray(d)), prob.tau1, (0.0, 0.9 * g[1]), "fp64")
+    sim.set_fields(prob.x0)
+    sim.step(steps)
+    prob.target = sim.mole_fractions()[:, 0].mean(axis=2)
+    sim.close()
+    return prob, d, g
+
+
+def test_inverse_problem_gradient_against_central_differences_at_full_size(evd):
+    """128 x 512, 2000 steps: every diffusivity component and g_y within 1e-4
+    relative of central differences (h = 1e-4 |theta_k|) of the loss of the
+    FP64 forward step (code independent of the adjoint)."""
+    prob, d, g = inverse_problem(2000)
+    loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
+    assert abs(loss - gpu_loss(prob, d, g)) <= 1e-12 * loss
+    for k in range(3):
+        h = 1e-4 * d[k]
+        dp, dm = list(d), list(d)
+        dp[k] += h
+        dm[k] -= h
+        fd = (gpu_loss(prob, dp, g) - gpu_loss(prob, dm, g)) / (2 * h)
+        assert abs(dd[k] - fd) <= 1e-4 * abs(fd), (k, dd[k], fd)
+    h = 1e-4 * abs(g[1])
+    fd = (gpu_loss(prob, d, (0.0, g[1] + h)) - gpu_loss(prob, d, (0.0, g[1] - h))) / (2 * h)
+    assert abs(dg[1] - fd) <= 1e-4 * abs(fd), (dg[1], fd)
+
+
+def test_adjoint_dot_product_along_seeded_directions(evd):
+    """<grad L, v> against the directional central difference of the FP64
+    forward loss along seeded unit directions v in (D12, D13, D23, g_y),
+    scaled by the parameters: agreement within 1e-4 relative."""
+    prob, d, g = inverse_problem(1000)
+    loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
+    theta = np.array(list(d) + [g[1]])
+    grad = np.concatenate([dd, [dg[1]]])
+    u = W.uniform01(1500, 8).reshape(2, 4) * 2.0 - 1.0
+    for v in u:
+        v = v / np.linalg.norm(v) * theta          # direction scaled by the parameters
+        eps = 1e-4
+        lp = gpu_loss(prob, list(theta[:3] + eps * v[:3]), (0.0, theta[3] + eps * v[3]))
+        lm = gpu_loss(prob, list(theta[:3] - eps * v[:3]), (0.0, theta[3] - eps * v[3]))
+        fd = (lp - lm) / (2 * eps)
+        assert abs(float(grad @ v) - fd) <= 1e-4 * abs(fd), (float(grad @ v), fd)
+
+
+def test_fp32_forward_gradient_against_the_fp64_adjoint(evd):
+    """The FP32-forward mode (FP32 steps and recomputation, FP64 reverse
+    sweep) on the 128 x 512 tube, 2000 steps: its loss and gradient against
+    the FP64 adjoint's, normwise within 1e-3 relative (the FP32 trajectory's
+    mole fractions stay within ~1e-6 of the FP64 ones at this horizon)."""
+    prob, d, g = inverse_problem(2000)
+    l64, dd64, dg64 = ADJ.loss_and_gradient(prob, d, g)
+    prob.forward = "fp32"
+    l32, dd32, dg32 = ADJ.loss_and_gradient(prob, d, g)
+    g64 = np.concatenate([dd64, dg64[1:2]])
+    g32 = np.concatenate([dd32, dg32[1:2]])
+    assert abs(l32 - l64) <= 1e-3 * l64, (l32, l64)
+    assert np.linalg.norm(g32 - g64) <= 1e-3 * np.linalg.norm(g64), (g32, g64)

@@ -94,7 +94,7 @@ def test_loschmidt_ternary_gravity_full_grid(evd, precision):
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 def test_stratification_256_sampled_windows(evd, precision):
     """The 256^3 closed box in the launch configuration the benchmark times:
     after k steps, sampled nodes (corners, edges, faces, interior) against the
@@ -117,7 +117,7 @@ def test_stratification_256_sampled_windows(evd, precision):
         rg = rho[:, c[2], c[1], c[0]]
         tol = 1e-12 if precision == "fp64" else TOL_X[precision]
         assert np.abs(xg - xo).max() < tol, (c, xg, xo)
-        assert max_rel(rg, ro) < (1e-12 if precision == "fp64" else 1e-5), (c, rg, ro)
+        assert max_rel(rg, ro) < {"fp64": 1e-12, "fp32": 1e-5, "fp16": 2e-3}[precision], (c, rg, ro)
     m0 = np.array([(wl.x[i] * wl.M[i]).sum() for i in range(3)])
     assert max_rel(sim.species_mass(), m0) < TOL_MASS[precision]
     sim.close()
