@@ -62,6 +62,33 @@ NCU_TRAFFIC = {
 }
 
 
+# Floating-point operations per species-site update of a step kernel, from
+# the ncu thread-instruction counters of one launch (dadd + dmul + 2 dfma for
+# double; fadd + fmul + 2 ffma, doubled for the f32x2 forms, for float), keyed
+# like NCU_TRAFFIC.  They place the compute-bound paths on their arithmetic
+# roof.
+NCU_FLOPS = {}
+
+
+def flops_for(digest: str, workload: str, precision: str):
+    return NCU_FLOPS.get((digest, workload, precision))
+
+
+def measure_alu_peaks(torch, dev, stream, device_id) -> dict:
+    """Arithmetic throughput of this GPU: the FMA-chain kernel in double,
+    float and float pairs (CUDA events), with the SM clock sampled meanwhile."""
+    from paper_2504_07059_gb300 import evd
+    out = {}
+    with ClockSampler(device_id) as clocks:
+        for name, kind, iters in (("fp64", 0, 1 << 15), ("fp32", 1, 1 << 20), ("fp32x2", 2, 1 << 19)):
+            flops, ms = evd.evd_fma_rate(kind, iters, stream)
+            out[name + "_tflops"] = flops / (ms * 1e-3) / 1e12
+    out["clocks"] = clocks.summary()
+    out["how"] = ("8 independent FMA chains per thread, 8 blocks of 256 threads per SM, one launch timed with "
+                  "CUDA events after a warm-up launch")
+    return out
+
+
 # The sources that define the step kernels and their launch configuration
 # (the device code, the TMA step, the launchers and the FP32/FP16 D3Q19 units).
 KERNEL_SOURCES = ("evd_device.cuh", "evd_tma.cuh", "evd_tma_launch.cuh", "evd_launch.cuh",
@@ -668,6 +695,16 @@ def run_ours(args) -> None:
         s64.close()
         fp64 = {"ms_per_step": ms64, "value": ns * nsites / (ms64 * 1e-3) / 1e9, "unit": UNIT,
                 "steps": n64, "speedup": ms64 / (ms / args.steps)}
+        # the FP64 step against the double-precision arithmetic roof
+        alu = measure_alu_peaks(torch, dev, stream, gpu_device_id(torch, local))
+        f64 = flops_for(kernel_digest(), args.workload, "fp64")
+        fp64["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": alu["fp64_tflops"],
+                            "peak_source": "measured (evd_fma_rate, double FMA chains)",
+                            "flops_per_ssu": f64,
+                            "achieved": None if f64 is None else f64 * ns * nsites / (ms64 * 1e-3) / 1e12}
+        if f64 is not None:
+            fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / alu["fp64_tflops"]
+        fp64["alu_peaks"] = alu
 
     # the other storage and the batched sweep, measured after the headline's
     # timed region: FP16 storage on the same workload, and the 512-tube sweep
@@ -677,6 +714,12 @@ def run_ours(args) -> None:
         extras["fp16"] = measure_single(torch, dev, stream, wl, "fp16", x_dev, min(args.steps, 300), 5)
         if fp64 is not None:
             extras["fp16"]["speedup_over_fp64"] = fp64["ms_per_step"] / extras["fp16"]["ms_per_step"]
+            f32 = flops_for(kernel_digest(), args.workload, "fp16")
+            peak32 = max(fp64["alu_peaks"]["fp32_tflops"], fp64["alu_peaks"]["fp32x2_tflops"])
+            if f32 is not None:
+                a32 = f32 * ns * nsites / (extras["fp16"]["ms_per_step"] * 1e-3) / 1e12
+                extras["fp16"]["alu"] = {"bound": "alu", "unit": "TFLOP/s", "flops_per_ssu": f32, "achieved": a32,
+                                         "peak": peak32, "frac": a32 / peak32}
         r = measure_tubes(torch, dev, stream, "fp32", min(args.steps, 300), 5, e2e=False, fp64=True)
         extras["tubes"] = {"workload": tubes_config()["workload"], "precision": "fp32",
                            "ms_per_step": r["ms_per_step"], "value": r["value"], "unit": UNIT,

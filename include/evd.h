@@ -365,6 +365,17 @@ evd_status evd_get_target_mass(evd_ctx* ctx, double* m_host);
 evd_status evd_population_mass_noalloc(const double* f_dev, int n_species, int q,
                                        long long nsites, double* m_dev, void* cuda_stream);
 
+/* Arithmetic throughput of the current GPU (not in the paper; the roofline
+ * of the FP64 step, which double-precision arithmetic bounds on this part):
+ * 8 independent fused multiply-add chains per thread, iters links each, on 8
+ * blocks of 256 threads per SM, timed with CUDA events on cuda_stream after
+ * one warm-up launch.  kind 0: double FMA; 1: float FMA; 2: float pairs
+ * (f32x2 FMA).  Returns the flops of the timed launch (2 per FMA and lane)
+ * and its milliseconds; the rate at the clock the GPU ran is flops / ms.
+ * Allocates and frees a small output array.  EVD_ERR_ARG for an unknown
+ * kind or iters outside 1 .. 2^24; evd_last_error(NULL) describes errors. */
+evd_status evd_fma_rate(int kind, int iters, double* flops, double* ms, void* cuda_stream);
+
 /* Release the context and all memory the library allocated for it. */
 evd_status evd_destroy(evd_ctx* ctx);
 

@@ -239,19 +239,40 @@ void fill_params(HostParams& h, const evd_grid* g, const evd_species* s)
         h.wl[2] = grid24(h.wl[2]);
         h.wl[0] = 1.0 - n1 * h.wl[1] - n2 * h.wl[2];
     }
+    // The lattice's second moment m2 = sum_a w_a e_ax^2 (1/3 for both
+    // lattices; with grid-rounded weights it is 1/3 + O(1e-8)).
+    const double m2 = !on_grid ? 1.0 / 3.0
+                               : (g->lattice == EVD_D2Q9 ? 2.0 * h.wl[1] + 4.0 * h.wl[2] : 2.0 * h.wl[1] + 8.0 * h.wl[2]);
     const double M1 = s->molar_mass[0];
     const double cs2_1 = 1.0 / 3.0;
     for (int i = 0; i < h.ns; ++i) {
         const double Mi = s->molar_mass[i];
         const double c = std::sqrt(M1 / Mi);
-        const double cs2 = c * c / 3.0;
-        const double tau = 0.5 + (s->tau1 - 0.5) * (cs2_1 / cs2);
+        const double cs2_ref = c * c / 3.0;
+        const double tau = 0.5 + (s->tau1 - 0.5) * (cs2_1 / cs2_ref);
         h.M[i] = Mi;
         h.Minv[i] = 1.0 / Mi;
         h.c[i] = c;
         h.unit[i] = (c == 1.0) ? 1 : 0;
-        h.inv_cs2[i] = 1.0 / cs2;
-        h.c_inv_cs2[i] = c / cs2;
+        h.inv_cs2[i] = 1.0 / cs2_ref;
+        h.c_inv_cs2[i] = c / cs2_ref;
+        h.c_inv_cs2_lo[i] = 0.0;
+        if (on_grid) {
+            // The collision keeps the species momentum sum_a e_a f_a only if
+            // c k m2 = 1, k = c / c_s^2 the factor of e.u in the equilibrium
+            // (sum_a e_a f^eq_a = rho u c k m2 with u = c j / rho).  With
+            // float c and k and the rounded weights c k m2 - 1 is up to
+            // ~5e-7, and every collision scales the momentum by that much:
+            // over 10^4 steps slow pressure waves grow or decay by ~1e-3 and
+            // move a diffusion front by a few 1e-5 in mole fraction.  So k =
+            // 1 / (c m2) for the float c, held as a float pair k_hi + k_lo
+            // (c k m2 = 1 to ~1e-14), and c_s^2 = c^2 m2.
+            const double cf = (double)(float)c;
+            const double k = 1.0 / (cf * m2);
+            h.c_inv_cs2[i] = (double)(float)k;
+            h.c_inv_cs2_lo[i] = (double)(float)(k - h.c_inv_cs2[i]);
+            h.inv_cs2[i] = 1.0 / (cf * cf * m2);
+        }
         h.tau_inv[i] = grid24(1.0 / tau);
         h.omt[i] = on_grid ? 1.0 - h.tau_inv[i] : 1.0 - 1.0 / tau;
         h.sfac[i] = 1.0 - 1.0 / (2.0 * tau);

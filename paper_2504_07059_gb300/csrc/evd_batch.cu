@@ -62,6 +62,7 @@ struct evd_batch {
     double* part;       // [items][MAXS] per-item mass partials
     size_t part_cap;
     double* small;      // target, corr[0], corr[1], mass_out: [n][MAXS] each
+    unsigned* seed_ctr; // {step counter, CTAs done} seeding the dithered rounding (in small)
     double *target, *corr[2], *mass_out;
     unsigned* err_flag;
     int mc_every, corr_pending, corr_applied;
@@ -161,7 +162,8 @@ namespace {
 
 BatchArgs args_of(const evd_batch* b)
 {
-    return BatchArgs{b->items_d, b->n_items, b->params_d, b->info_d, b->grid};
+    return BatchArgs{b->items_d, b->n_items, b->params_d, b->info_d, b->grid,
+                     b->precision == EVD_FP64 ? nullptr : b->seed_ctr};
 }
 
 cudaError_t dispatch_step(const evd_batch* b, cudaStream_t st, const void* fin, void* fout, int flags,
@@ -473,6 +475,7 @@ evd_status evd_batch_create(int lattice, int precision, const evd_member* member
     b->corr[1] = b->small + 2 * arr;
     b->mass_out = b->small + 3 * arr;
     b->err_flag = (unsigned*)(b->small + 4 * arr);
+    b->seed_ctr = (unsigned*)((char*)(b->small + 4 * arr) + 128);
     evd_status s = set_schedule(b, 512, 8);
     if (s == EVD_OK) s = upload_params(b);
     if (s == EVD_OK) {
@@ -535,6 +538,7 @@ evd_status evd_batch_set_fields(evd_batch* b, const double* x, const double* n)
         if (s != EVD_OK) return s;
     }
     BK(b, cudaMemsetAsync(b->err_flag, 0, sizeof(unsigned), b->stream));
+    BK(b, cudaMemsetAsync(b->seed_ctr, 0, 2 * sizeof(unsigned), b->stream));   // step t + 1 draws seed t + 1
     b->launches += 1;
     BK(b, dispatch_init(b, xd, nd));
     b->cur = 0;
@@ -672,9 +676,10 @@ evd_status evd_batch_autotune(evd_batch* b, int steps_per_trial, int* item_sites
     if (steps_per_trial < 2 || steps_per_trial > 64 || steps_per_trial % 2 != 0)
         return fail(b, EVD_ERR_ARG, "steps_per_trial must be even, 2..64");
     DeviceGuard dg(b->device);
-    // the trials step a copy of the populations; the state is put back after
+    // the trials step a copy of the populations and of the dither step
+    // counter; both are put back after
     void* backup = nullptr;
-    BK(b, cudaMalloc(&backup, 2 * b->buf_bytes));
+    BK(b, cudaMalloc(&backup, 2 * b->buf_bytes + 16));
     char* bk = (char*)backup;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     evd_status r = EVD_OK;
@@ -682,6 +687,7 @@ evd_status evd_batch_autotune(evd_batch* b, int steps_per_trial, int* item_sites
     float best_ms = 1e30f;
     cudaError_t e = cudaMemcpyAsync(bk, b->buf[0], b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bk + b->buf_bytes, b->buf[1], b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bk + 2 * b->buf_bytes, b->seed_ctr, 8, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) r = cuda_fail(b, e, "autotune setup");
@@ -722,6 +728,7 @@ evd_status evd_batch_autotune(evd_batch* b, int steps_per_trial, int* item_sites
     if (r == EVD_OK) r = r2;
     e = cudaMemcpyAsync(b->buf[0], bk, b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->buf[1], bk + b->buf_bytes, b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->seed_ctr, bk + 2 * b->buf_bytes, 8, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess && r == EVD_OK) r = cuda_fail(b, e, "autotune restore");
     if (e0) cudaEventDestroy(e0);

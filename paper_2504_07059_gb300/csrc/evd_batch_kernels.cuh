@@ -44,30 +44,20 @@ __device__ __forceinline__ void load_params(Params<T>& dst, const Params<T>* __r
 }
 
 // One time step of one work item: sites [node0, node0 + count) of a member
-// whose populations start at fin / fout.  Not inlined: it runs once per item,
+// whose populations start at fin / fout (the single-lattice step's node
+// code, dithered rounding included).  Not inlined: it runs once per item,
 // and three inlined species counts per kernel make D3Q19 compile very slowly.
 template <int LAT, int NS, typename S, typename T>
 __device__ __noinline__ void item_step(const Params<T>& p, const S* __restrict__ fin, S* __restrict__ fout,
                                           int node0, int count, double* __restrict__ part, unsigned& err,
                                           int flags, const double* __restrict__ corr)
 {
-    constexpr int Q = Lat<LAT>::Q;
     double m[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) m[i] = 0.0;
     for (int node = node0 + threadIdx.x; node < node0 + count; node += BLOCK) {
-        T f[NS][Q];
-        T gn[3];   // specific body force at this node
-        node_force(p, node, gn);
         NodeState<NS, T> s;
-        const Nbr nb = neighbours(p, node);
-        T R0[NS];
-        node_base<LAT, NS>(p, fin, node, R0);
-        gather_all<LAT, NS>(p, fin, node, nb, R0, f);
-        if (corr) add_correction<LAT, NS>(p, corr, f, R0);
-        moments<LAT, NS, dev_arith<S>()>(p, f, s, err, gn, R0);
-        collide<LAT, NS, dev_arith<S>(), false, Codec<S>::NODE>(p, f, s, gn);
-        store_all<LAT, NS>(p, fout, node, f, s.rho, R0);
+        step_node<LAT, NS>(p, fin, fout, node, corr, s, err);
 #pragma unroll
         for (int i = 0; i < NS; ++i) m[i] += (double)s.rho[i];
     }
@@ -83,15 +73,19 @@ __global__ void __launch_bounds__(BLOCK, 6)
 k_step_batch(const BatchItem* __restrict__ items, int n_items, const Params<T>* __restrict__ params,
              const MemberInfo* __restrict__ info, const S* __restrict__ fin, S* __restrict__ fout,
              double* __restrict__ part, unsigned* __restrict__ err_flag, int flags,
-             const double* __restrict__ corr)
+             const double* __restrict__ corr, unsigned* __restrict__ seed)
 {
     __shared__ Params<T> sp;
     unsigned err = 0;
+    // reduced storage: the step's seed of the dithered rounding, from the
+    // device step counter seed[0] (read before this CTA counts itself done)
+    const unsigned step_seed = seed ? (unsigned)((unsigned long long)(*(volatile unsigned*)seed + 1u) * 2654435761ull) | 1u : 0u;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const BatchItem w = items[it];
         const long long off = info[w.member].foff;
         __syncthreads();   // the previous item is done with sp
         load_params(sp, params + w.member);
+        if (seed && threadIdx.x == 0) sp.seed = step_seed;
         __syncthreads();
         const double* c = corr ? corr + (long long)w.member * MAXS : nullptr;
         double* pt = part + (long long)it * MAXS;
@@ -102,6 +96,17 @@ k_step_batch(const BatchItem* __restrict__ items, int n_items, const Params<T>* 
         }
     }
     if (err) atomicOr(err_flag, err);
+    if (seed) {   // the last CTA to finish advances the step counter for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(seed + 1, 1u) == gridDim.x - 1) {
+                seed[1] = 0u;
+                seed[0] += 1u;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // Observables of one work item (as k_readout), written into the
@@ -249,7 +254,7 @@ cudaError_t batch_step(const BatchArgs& a, const void* fin, void* fout, double* 
 {
     if (a.n_items == 0) return cudaSuccess;
     k_step_batch<LAT, S, T><<<a.grid, BLOCK, 0, st>>>(a.items, a.n_items, (const Params<T>*)a.params, a.info,
-                                                      (const S*)fin, (S*)fout, part, err, flags, corr);
+                                                      (const S*)fin, (S*)fout, part, err, flags, corr, a.seed);
     return cudaGetLastError();
 }
 

@@ -138,6 +138,7 @@ struct Params {
     T c[MAXS];             // lattice speed c_i = sqrt(M_1 / M_i)
     T inv_cs2[MAXS];       // 1 / c_s,i^2 = 3 / c_i^2
     T c_inv_cs2[MAXS];     // c_i / c_s,i^2 = 3 / c_i
+    T c_inv_cs2_lo[MAXS];  // float arithmetic: c_inv_cs2 + c_inv_cs2_lo = 1 / (c_i m2) (0 in double)
     T tau_inv[MAXS];       // 1 / tau_i
     T omt[MAXS];           // 1 - 1/tau_i
     T sfac[MAXS];          // 1 - 1/(2 tau_i)
@@ -169,6 +170,7 @@ inline Params<T> to_params(const HostParams& h)
     for (int i = 0; i < MAXS; ++i) {
         p.unit[i] = h.unit[i];
         p.c[i] = (T)h.c[i]; p.inv_cs2[i] = (T)h.inv_cs2[i]; p.c_inv_cs2[i] = (T)h.c_inv_cs2[i];
+        p.c_inv_cs2_lo[i] = (T)h.c_inv_cs2_lo[i];
         p.tau_inv[i] = (T)h.tau_inv[i]; p.omt[i] = (T)h.omt[i]; p.sfac[i] = (T)h.sfac[i];
         p.Minv[i] = (T)h.Minv[i]; p.M[i] = (T)h.M[i];
         for (int j = 0; j < MAXS; ++j) { p.MM[i][j] = (T)h.MM[i][j]; p.iD[i][j] = (T)h.iD[i][j]; }
@@ -877,6 +879,12 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
                                         unsigned h0 = 0)
 {
     constexpr int Q = Lat<LAT>::Q;
+    // k x for k = c_i / c_s,i^2 (with its low part in float arithmetic, so
+    // that the equilibrium carries exactly the species momentum)
+    auto kmul = [&](int i, T x) -> T {
+        if constexpr (std::is_same<T, float>::value) return fmaf(p.c_inv_cs2[i], x, p.c_inv_cs2_lo[i] * x);
+        else return p.c_inv_cs2[i] * x;
+    };
     // f <- f + X (deviation arithmetic): minus the reference shift, plus the
     // dither, in the single rounding of the last addition
     auto upd = [&](int i, int a, int c, T X) -> T {
@@ -935,7 +943,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const T ea = edot<LAT, A>(av[i]);
-            const T t1 = p.c_inv_cs2[i] * eu;                       // e.u / c_s^2
+            const T t1 = kmul(i, eu);                               // e.u / c_s^2
             T S = p.wl[C] * sr[i] * fma(p.c[i] * eg, (T)1 + t1, -ug);
             if constexpr (CORR) {
                 const T eX = edot<LAT, A>(Xc[i]), eY = edot<LAT, A>(Yc[i]);
@@ -949,7 +957,7 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
             }
             if constexpr (DA) {
                 const T phi = fma(t1, fma((T)0.5, t1, (T)1), U2[i]);
-                const T b = fma(p.c_inv_cs2[i], ea, Bm[i]);
+                const T b = kmul(i, ea) + Bm[i];
                 const T B = p.tau_inv[i] + b;
                 f[i][A] = upd(i, A, C, fma(p.tau_inv[i], dt[i][C] - f[i][A], fma(wr[i][C], fma(phi, B, b), S)));
             } else {
@@ -975,8 +983,8 @@ __device__ __forceinline__ void collide(const Params<T>& p, T (&f)[NS][Lat<LAT>:
             const T eg = edot<LAT, A>(g);
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-                const T t1 = p.c_inv_cs2[i] * eu;
-                const T bO = p.c_inv_cs2[i] * edot<LAT, A>(av[i]);
+                const T t1 = kmul(i, eu);
+                const T bO = kmul(i, edot<LAT, A>(av[i]));
                 const T ceg = p.c[i] * eg;
                 const T phiE = fma((T)0.5 * t1, t1, U2[i]);
                 const T K = p.wl[C] * sr[i];

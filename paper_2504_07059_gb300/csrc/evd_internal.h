@@ -32,6 +32,7 @@ struct HostParams {
     int wall[3];
     int unit[MAXS];
     double c[MAXS], inv_cs2[MAXS], c_inv_cs2[MAXS];
+    double c_inv_cs2_lo[MAXS];   // float arithmetic: c_inv_cs2 + c_inv_cs2_lo = 1 / (c m2) (0 in FP64)
     double tau_inv[MAXS], omt[MAXS], sfac[MAXS];
     double Minv[MAXS], M[MAXS];
     double MM[MAXS][MAXS], iD[MAXS][MAXS];
@@ -95,6 +96,7 @@ struct BatchArgs {
     const void* params;      // Params<T>[members] on the device
     const MemberInfo* info;  // [members] on the device
     int grid;                // CTAs of the step launch (persistent when < n_items)
+    unsigned* seed;          // {step counter, CTAs done}: seeds the dithered rounding, or nullptr
 };
 
 template <int PREC, int LAT>

@@ -375,7 +375,7 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
 #pragma unroll
     for (int a = 0; a < 3; ++a) w[a] = p.w1[sp][a];
     const WPair wp = weight_pairs(w);
-    const float csp = p.c[sp], inv_cs2 = p.inv_cs2[sp], c_inv_cs2 = p.c_inv_cs2[sp];
+    const float csp = p.c[sp], inv_cs2 = p.inv_cs2[sp], c_inv_cs2 = p.c_inv_cs2[sp], c_inv_lo = p.c_inv_cs2_lo[sp];
     const float tau_inv = p.tau_inv[sp], omt = p.omt[sp];
     const float isf = inv_cs2 * p.sfac[sp];
     const bool xlo = p.wall[0] && x == 0, xhi = p.wall[0] && x == p.nx - 1;
@@ -428,27 +428,57 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         // registers are live, into this iteration's half of the term buffer;
         // they join the node's gathered values next iteration.
         if (ok && wall_next) {
-            const int zc_next = zwall ? (k == 0 ? 1 : (k == p.nz - 1 ? 2 : 0)) : 0;   // z wall class
-            const float4* L = lumps + ((wcls_xy + 9 * zc_next) * NS + sp) * Q;
+            const bool zw = zwall && (k == 0 || k == p.nz - 1);
+            const bool xw = xlo || xhi, yw = ylo || yhi;
             float* cw = reinterpret_cast<float*>(smem + G::cen_offset) + (idx & 1) * Q * G::threads + threadIdx.x;
-            static_for<0, NP>([&](auto kc) {
-                constexpr int K = decltype(kc)::value;
-                constexpr int A = 2 * K + 1, B = A + 1;
-                const float4 la = __ldg(L + A), lb = __ldg(L + B);
-                float ca = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
-                float cb = tile_center<B, NS, S, TY, SLOTS>(base, sp, tx, ty);
-                if constexpr (G::LOCAL) {   // decoded with the node's density
-                    const float wa = p.wl[wclass<1>(A)];
-                    ca = fmaf(wa, rd[1][1], ca);
-                    cb = fmaf(wa, rd[1][1], cb);
-                    cw[A * G::threads] = la.x * ca + la.y * cb;
-                    cw[B * G::threads] = lb.x * cb + lb.y * ca;
-                } else {   // deviations, plus the reference the weights carry
-                    const float ref = p.ref[sp][wclass<1>(A)];
+            // the node's own population of direction a, decoded (half storage)
+            auto own = [&](auto ac) -> float {
+                constexpr int A = decltype(ac)::value;
+                const float c = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
+                if constexpr (G::LOCAL) return fmaf(p.wl[wclass<1>(A)], rd[1][1], c);
+                else return c;
+            };
+            if ((int)xw + (int)yw + (int)zw == 1) {
+                // one flat wall (the common case): with w = (w0, w1, w2) the
+                // species' 1-D weights, a direction moving away from the wall
+                // keeps its own weight w2 that crossed it (L_self = w2), takes
+                // its opposite's crossing weight w0 (L_opp = w0), and carries
+                // K - 1 = w2; the direction heading into the wall carries
+                // K - 1 = -w2; directions along the wall have none.  The host
+                // table holds the same coefficients for every wall class.
+                const int kd = xw ? 0 : (yw ? 1 : 2);
+                const bool at_hi = xw ? xhi : (yw ? yhi : k == p.nz - 1);
+                const float w0 = w[0], w2 = w[2];
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    constexpr int A = 2 * K + 1, B = A + 1;
+                    const int e = kd == 0 ? ev<1>(A, 0) : (kd == 1 ? ev<1>(A, 1) : ev<1>(A, 2));
+                    const int away = at_hi ? -e : e;   // +1: A leaves the wall, -1: A heads into it
+                    float ta = 0.0f, tb = 0.0f;
+                    if (away != 0) {
+                        const float ca = own(std::integral_constant<int, A>{});
+                        const float cb = own(std::integral_constant<int, B>{});
+                        const float ref = G::LOCAL ? 0.0f : p.ref[sp][wclass<1>(A)];
+                        if (away > 0) { ta = w2 * ca + w0 * cb + ref * w2; tb = ref * -w2; }
+                        else { ta = ref * -w2; tb = w2 * cb + w0 * ca + ref * w2; }
+                    }
+                    cw[A * G::threads] = ta;
+                    cw[B * G::threads] = tb;
+                });
+            } else {   // edges and corners: the host table of the wall class
+                const int zc_next = zwall ? (k == 0 ? 1 : (k == p.nz - 1 ? 2 : 0)) : 0;
+                const float4* L = lumps + ((wcls_xy + 9 * zc_next) * NS + sp) * Q;
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    constexpr int A = 2 * K + 1, B = A + 1;
+                    const float4 la = __ldg(L + A), lb = __ldg(L + B);
+                    const float ca = own(std::integral_constant<int, A>{});
+                    const float cb = own(std::integral_constant<int, B>{});
+                    const float ref = G::LOCAL ? 0.0f : p.ref[sp][wclass<1>(A)];
                     cw[A * G::threads] = la.x * ca + la.y * cb + ref * la.z;
                     cw[B * G::threads] = lb.x * cb + lb.y * ca + ref * lb.z;
-                }
-            });
+                });
+            }
         }
         float f0;
         float2 F[NP];
@@ -659,7 +689,10 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const float U2 = DA ? -0.5f * inv_cs2 * usq : fmaf(-0.5f * inv_cs2, usq, 1.0f);
         float U[3], Av[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) { U[d] = c_inv_cs2 * u[d]; Av[d] = c_inv_cs2 * av[d]; }
+        for (int d = 0; d < 3; ++d) {   // k = c / c_s^2 as k_hi + k_lo: exact species momentum
+            U[d] = fmaf(c_inv_cs2, u[d], c_inv_lo * u[d]);
+            Av[d] = fmaf(c_inv_cs2, av[d], c_inv_lo * av[d]);
+        }
         const float sr = rho * isf;
         float wr[3], Kc[3], Cc[3];
 #pragma unroll

@@ -97,6 +97,8 @@ _SIGNATURES = {
     "evd_get_reference_mode": (ctypes.c_int, [_vp]),
     "evd_get_target_mass": (_st, [_vp, _vp]),
     "evd_population_mass_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _vp]),
+    "evd_fma_rate": (_st, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           _vp]),
     "evd_destroy": (_st, [_vp]),
     "evd_last_error": (ctypes.c_char_p, [_vp]),
     # include/evd_batch.h
@@ -637,3 +639,11 @@ class Batch:
 
     def check(self):
         evd_batch_check(self.b)
+
+
+def evd_fma_rate(kind: int, iters: int = 1 << 16, stream=None):
+    """(flops, milliseconds) of the FMA-chain throughput kernel: kind 0
+    double, 1 float, 2 float pairs."""
+    f, m = ctypes.c_double(), ctypes.c_double()
+    _check(lib().evd_fma_rate(int(kind), int(iters), ctypes.byref(f), ctypes.byref(m), _stream(stream)))
+    return f.value, m.value
