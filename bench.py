@@ -15,8 +15,9 @@ time / 1e9, whole job over all ranks.  Every rank runs an independent replica
 (the path is single-GPU; there is no data-path collective), so scaling is weak.
 
 ``--workload adjoint`` times instead the loss and exact gradient of the
-mole-fraction misfit (evd_loss_gradient, FP64) over ``--steps`` steps of the
-128 x 512 ternary D2Q9 tube with gravity of the inverse problem, one GPU.
+mole-fraction misfit (evd_loss_gradient, FP64 reverse sweep) over a horizon of
+``--horizon`` steps (20000) of the 128 x 512 ternary D2Q9 tube with gravity of
+the inverse problem, one GPU, with the FP64 and the FP32 forward pass.
 
 Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead (the paper publishes no
@@ -528,23 +529,27 @@ def measure_single(torch, dev, stream, wl, prec: str, x_dev, steps: int, warmup:
 def run_adjoint(args, torch, dev) -> None:
     """Loss and gradient per step of the horizon: forward steps with
     checkpoints, recomputation and the reverse sweep, through the C ABI call
-    (host inputs and outputs, allocations included), for the hand-written
-    reverse sweep and the dual-number cross-check; the FP64 forward step on
-    the same lattice beside them (CUDA events)."""
+    (host inputs and outputs, allocations included), over ``--horizon`` steps
+    with the FP64 and with the FP32 forward pass; the dual-number cross-check
+    over a shorter horizon; the FP64 forward step on the same lattice beside
+    them (CUDA events)."""
     from paper_2504_07059_gb300 import adjoint as ADJ, evd
     wl = W.loschmidt_ternary_gravity(nx=128, ny=512)
-    nsteps = args.steps
+    nsteps = args.horizon
     d = [wl.D[0, 1], wl.D[0, 2], wl.D[1, 2]]
     g = (0.0, wl.g[1])
     stream = torch.cuda.current_stream(dev)
-    # target: the same run with every diffusivity x 1.1 and the force x 0.9
-    sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, 1.1 * wl.D, wl.tau1,
-                         (0.0, 0.9 * wl.g[1]), "fp64", stream)
-    sim.set_fields(wl.x)
-    sim.step(nsteps)
-    target = sim.mole_fractions()[:, 0].mean(axis=2)
-    sim.close()
-    prob = ADJ.Problem(wl.shape[:2], wl.wall_mask, wl.M, wl.tau1, wl.x, target, nsteps)
+
+    def problem(n, mode=evd.EVD_ADJOINT_REVERSE, forward="fp64"):
+        # target: the same run with every diffusivity x 1.1 and the force x 0.9
+        sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, 1.1 * wl.D, wl.tau1,
+                             (0.0, 0.9 * wl.g[1]), "fp64", stream)
+        sim.set_fields(wl.x)
+        sim.step(n)
+        target = sim.mole_fractions()[:, 0].mean(axis=2)
+        sim.close()
+        return ADJ.Problem(wl.shape[:2], wl.wall_mask, wl.M, wl.tau1, wl.x, target, n, mode=mode, forward=forward)
+
     sim = evd.Simulation(wl.lattice, wl.shape, wl.wall_mask, wl.M, wl.D, wl.tau1, wl.g, "fp64", stream)
     sim.set_fields(wl.x)
     evd.evd_step(sim.ctx, args.warmup)
@@ -557,30 +562,41 @@ def run_adjoint(args, torch, dev) -> None:
     sim.check()
     fwd_ms = e0.elapsed_time(e1) / nsteps
     sim.close()
-    res = {}
-    for name, mode in (("reverse", evd.EVD_ADJOINT_REVERSE), ("dual", evd.EVD_ADJOINT_DUAL)):
-        prob.mode = mode
+
+    def timed(prob):
         warm = ADJ.Problem(prob.shape, prob.wall_mask, prob.molar_mass, prob.tau1, prob.x0, prob.target,
-                           args.warmup, mode=mode)
+                           args.warmup, mode=prob.mode, forward=prob.forward)
         ADJ.loss_and_gradient(warm, d, g)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         loss, dd, dg = ADJ.loss_and_gradient(prob, d, g)
-        res[name] = ((time.perf_counter() - t0) * 1e3 / nsteps, loss, dd, dg)
-    ms = res["reverse"][0]
-    rel = float(np.max(np.abs(np.concatenate(res["reverse"][2:]) - np.concatenate(res["dual"][2:])) /
-                       np.abs(np.concatenate(res["dual"][2:]))))
+        return (time.perf_counter() - t0) * 1e3 / prob.nsteps, loss, np.concatenate([dd, dg])
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    full = problem(nsteps)
+    ms, loss, grad = timed(full)
+    full.forward = "fp32"
+    ms32, loss32, grad32 = timed(full)
+    nshort = min(nsteps, args.dual_horizon)
+    short = problem(nshort)
+    ms_rs, _, grad_rs = timed(short)
+    short.mode = evd.EVD_ADJOINT_DUAL
+    ms_dual, _, grad_dual = timed(short)
     ssu = wl.ns * wl.nsites
     print(json.dumps({
         "metric": "adjoint species-site updates/s (GLUPS)", "value": ssu / (ms * 1e-3) / 1e9, "unit": UNIT,
         "n_gpus": 1, "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "inverse-problem tube 128x512 ternary D2Q9, gravity, loss + gradient "
-                               "w.r.t. 3 D_ij and g", "checkpoint_every": "ceil(sqrt(steps))"},
+                               "w.r.t. 3 D_ij and g", "horizon": nsteps, "checkpoint_every": "ceil(sqrt(steps))"},
         "forward_fp64_ms_per_step": fwd_ms, "reverse_over_forward": ms / fwd_ms,
-        "dual_ms_per_step": res["dual"][0], "reverse_vs_dual_max_rel_diff": rel,
-        "loss": res["reverse"][1], "dL_dD": list(map(float, res["reverse"][2])),
-        "dL_dg": list(map(float, res["reverse"][3])),
+        "loss": loss, "dL_dD": list(map(float, grad[:3])), "dL_dg": list(map(float, grad[3:])),
+        "fp32_forward": {"ms_per_step": ms32, "loss_rel_diff": abs(loss32 - loss) / abs(loss),
+                         "grad_max_rel_diff": rel(grad32, grad)},
+        "dual_check": {"horizon": nshort, "reverse_ms_per_step": ms_rs, "dual_ms_per_step": ms_dual,
+                       "max_rel_diff": rel(grad_rs, grad_dual)},
     }), flush=True)
 
 
@@ -781,7 +797,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 step for comparison")
     ap.add_argument("--members", type=int, default=512, help="tubes workload: the first N tubes of the sweep")
     ap.add_argument("--schedule", default="", help="tubes workload: 'item_sites,ctas_per_sm' instead of autotuning")
-    ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (2 or 4)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per tile of the TMA step (1, 2 or 4)")
+    ap.add_argument("--horizon", type=int, default=20000, help="adjoint workload: steps of the loss horizon")
+    ap.add_argument("--dual-horizon", type=int, default=1000,
+                    help="adjoint workload: horizon of the dual-number cross-check")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP16-storage and batched-sweep measurements after the headline")
     args = ap.parse_args()

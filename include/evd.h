@@ -306,9 +306,9 @@ evd_status evd_set_adjoint_mode(evd_ctx* ctx, int mode);
  * t = 0 of the run.  EVD_ERR_ARG for another precision. */
 evd_status evd_set_adjoint_forward(evd_ctx* ctx, int precision);
 
-/* Rows per tile of the TMA-staged step: 1 (four CTAs of 3 warps per SM for
- * three species, each synchronising only the species of its row), 2 (the
- * default; two CTAs of 6 warps) or 4 (one CTA of 12 warps).  Same results;
+/* Rows per tile of the TMA-staged step: 1 (the default; four CTAs of 3 warps
+ * per SM for three species, each synchronising only the species of its
+ * row), 2 (two CTAs of 6 warps) or 4 (one CTA of 12 warps).  Same results;
  * a tuning knob.  Synchronises.  EVD_ERR_ARG where the TMA step does not
  * apply. */
 evd_status evd_set_tile_rows(evd_ctx* ctx, int rows);

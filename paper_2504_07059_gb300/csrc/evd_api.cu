@@ -24,7 +24,7 @@ namespace {
 constexpr int FLAG_MASS = 1, FLAG_RAW = 2;   // must match the device-side flags
 constexpr int BLOCK = 128;                   // must match the device-side block size
 constexpr long long PLANE_ALIGN = 64;        // elements; every plane starts 128-byte aligned
-constexpr int kTmaRows = 2;                  // default rows per tile of the TMA step
+constexpr int kTmaRows = 1;                  // default rows per tile of the TMA step
 
 thread_local std::string g_create_error;
 

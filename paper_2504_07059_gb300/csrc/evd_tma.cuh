@@ -24,13 +24,14 @@
 // the compute warps per iteration) for the cross collision, and each thread
 // collides and stores its own 19 populations.
 //
-// Walls: a thread's (x, y) column is fixed for the whole march, so solid
-// in-plane stencil nodes are removed once, by zeroing their weights; a z-slab
-// beyond a z wall contributes nothing.  Wall-adjacent nodes add the App. A
-// lumped terms f_a += L_self f*_a(O) + L_opp f*_abar(O), with the coefficients
-// of their wall class (which of the six walls they touch) from a table built
-// on the host, and their own populations f*(O) fetched from global memory at
-// the start of the iteration so that the loads overlap the interpolation.
+// Walls: a stencil node beyond a wall reads as zero (the fill of the tile
+// copy outside the lattice), so the full weights act as the weights of the
+// fluid nodes alone; a z-slab beyond a z wall contributes nothing.
+// Wall-adjacent nodes add the App. A lumped terms f_a += L_self f*_a(O) +
+// L_opp f*_abar(O), their own populations f*(O) being the centre of the
+// stage that holds their slab: the terms go into the node's running sums in
+// the iteration that reads that slab (closed form at a flat wall; the host
+// table of the wall class at edges and corners).
 // Periodic z is a wrapped slab coordinate; x and y must be walled (other
 // geometries use the general kernel).
 #pragma once
@@ -91,11 +92,7 @@ struct TmaLayout {
     }
     static constexpr int ring_bytes = SLOTS * slot_bytes;
     static constexpr int exch_bytes = 2 * NS * TY * TTX * 16;   // two float4 buffers
-    // App. A terms of wall nodes, [2][direction][thread] floats: written
-    // while the node's slab is resident, added one iteration later
-    static constexpr int cen_offset = ring_bytes + exch_bytes;
-    static constexpr int cen_bytes = 2 * 19 * threads * 4;
-    static constexpr int msum_offset = cen_offset + cen_bytes;
+    static constexpr int msum_offset = ring_bytes + exch_bytes;
     static constexpr int bar_offset = msum_offset + NS * TY * 8 + 8;
     static constexpr int total_bytes = bar_offset + SLOTS * 8 + 128;   // + alignment slack
 };
@@ -310,8 +307,39 @@ __device__ __forceinline__ float edot3(const float (&v)[3])
     return edot<1, A>(v);
 }
 
+// App. A terms of a node at an edge or corner (two or three walls) from the
+// host table of its wall class: t[a - 1] = L_self f*_a + L_opp f*_abar (+ the
+// reference the weights carry, float storage) for a = 1..18, f* the node's own
+// populations in this stage's tile (half storage: decoded with the node's
+// density rdc).  Out of line: such nodes are rare, and inlined, the table
+// loads would be scheduled early and hold registers across the interpolation.
 template <int NS, typename S, int TY, int SLOTS>
-__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 1 ? 4 : (TY == 2 ? 2 : 1))
+__device__ __noinline__ void wall_terms_table(const unsigned char* base, int sp, int tx, int ty,
+                                              const float4* __restrict__ L, float ref1, float ref2, float wl1,
+                                              float wl2, float rdc, float* __restrict__ t)
+{
+    using G = TmaLayout<NS, S, TY, SLOTS>;
+    static_for<0, 9>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        constexpr int A = 2 * K + 1, B = A + 1;
+        constexpr bool diag = wclass<1>(A) == 2;
+        const float4 la = __ldg(L + A), lb = __ldg(L + B);
+        float ca = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
+        float cb = tile_center<B, NS, S, TY, SLOTS>(base, sp, tx, ty);
+        float ref = 0.0f;
+        if constexpr (G::LOCAL) {
+            ca = fmaf(diag ? wl2 : wl1, rdc, ca);
+            cb = fmaf(diag ? wl2 : wl1, rdc, cb);
+        } else {
+            ref = diag ? ref2 : ref1;
+        }
+        t[A - 1] = la.x * ca + la.y * cb + ref * la.z;
+        t[B - 1] = lb.x * cb + lb.y * ca + ref * lb.z;
+    });
+}
+
+template <int NS, typename S, int TY, int SLOTS>
+__global__ void __launch_bounds__(TmaLayout<NS, S, TY, SLOTS>::threads, TY == 1 ? 5 : (TY == 2 ? 2 : 1))
 k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S* __restrict__ fin,
            S* __restrict__ fout, double* __restrict__ mass_part, unsigned* __restrict__ err_flag, int flags,
            const double* __restrict__ corr, const float4* __restrict__ lumps, int ntx, int nty, int zchunk,
@@ -412,7 +440,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const bool emit = zo >= zb && zo < ze;  // the same for every thread of the CTA
         const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
         const int node = x + p.nx * y + nxy * zo;
-        const bool wall_node = emit && active && (col_wall || zlo || zhi);
         // the node of this stage's slab, finished next iteration, at a wall
         const bool wall_next = !halo && active && (col_wall || (zwall && (k == 0 || k == p.nz - 1)));
         const bool ok = mbar_wait_bounded(full(slot), (unsigned)((idx / SLOTS) & 1), wait_polls);
@@ -421,22 +448,66 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         float rd[3][3] = {};
         if constexpr (G::LOCAL)
             if (ok) dens_block<NS, S, TY, SLOTS>(base, sp, tx, ty, rd);
-        // App. A terms of the wall node of this slab, from its own
-        // post-collision populations, which are in this stage's tile (the
-        // centre of every plane): L_self f*_a + L_opp f*_abar (+ the reference
-        // the weights carry, float storage).  Computed now, while few
-        // registers are live, into this iteration's half of the term buffer;
-        // they join the node's gathered values next iteration.
+        float f0 = accN0;
+        float2 F[NP];
+        if (ok) {
+            // The same running sums for every species; a unit-speed species
+            // (c = 1, weights (1, 0, 0)) reads each member's upstream node
+            // instead of interpolating (exact shift), and its z sums multiply
+            // by exactly one and zero.
+            float di[3][3] = {};   // [ey + 1][ex + 1]
+            if constexpr (G::LOCAL)
+                if (!unit)
+                    static_for<0, 9>([&](auto kc) {
+                        constexpr int K = decltype(kc)::value;
+                        di[K / 3][K % 3] = dens_interp<K % 3 - 1, K / 3 - 1>(rd, w);
+                    });
+            if (!halo) {
+                if constexpr (G::LOCAL) accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1][1], p.wl[0]);
+                else accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, 0.0f, 0.0f);
+            }
+            auto march = [&](auto uc) {
+                constexpr bool UNIT = decltype(uc)::value;
+                static_for<0, NP>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value;
+                    constexpr int A = 2 * K + 1, B = A + 1;
+                    constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1), ez = ev<1>(A, 2);
+                    const float wa = p.wl[wclass<1>(A)];
+                    auto slab = [&]() -> float2 {   // this slab's in-plane value of the pair
+                        if constexpr (UNIT)
+                            return make_float2(inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1 - ey][1 - ex], wa),
+                                               inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1 + ey][1 + ex], wa));
+                        else
+                            return inplane2<A, NS, S, TY, SLOTS>(base, sp, tx, ty, wp,
+                                                                 make_float2(di[ey + 1][ex + 1], di[1 - ey][1 - ex]), wa);
+                    };
+                    if constexpr (ez == 0) {
+                        F[K] = accN[K];
+                        if (!halo) accN[K] = slab();
+                    } else {
+                        const float2 R = slab();
+                        // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
+                        F[K] = pfma(wpo<ez>(wp, 1), R, accA[K]);
+                        accA[K] = pfma(wpo<ez>(wp, 0), R, accB[K]);
+                        accB[K] = pmul(wpo<ez>(wp, -1), R);
+                    }
+                });
+            };
+            if (unit) march(std::true_type{});
+            else march(std::false_type{});
+        }
+        // App. A terms of the wall node of this slab (finished next
+        // iteration), from its own post-collision populations, which are the
+        // centre of every plane of this stage's tile: L_self f*_a + L_opp
+        // f*_abar (+ the reference the weights carry, float storage), added
+        // to the node's running sums (accN: in-plane pairs, accA: z-moving).
         if (ok && wall_next) {
             const bool zw = zwall && (k == 0 || k == p.nz - 1);
             const bool xw = xlo || xhi, yw = ylo || yhi;
-            float* cw = reinterpret_cast<float*>(smem + G::cen_offset) + (idx & 1) * Q * G::threads + threadIdx.x;
-            // the node's own population of direction a, decoded (half storage)
-            auto own = [&](auto ac) -> float {
-                constexpr int A = decltype(ac)::value;
-                const float c = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
-                if constexpr (G::LOCAL) return fmaf(p.wl[wclass<1>(A)], rd[1][1], c);
-                else return c;
+            auto add_term = [&](auto kc, float2 v) {
+                constexpr int K = decltype(kc)::value;
+                if constexpr (ev<1>(2 * K + 1, 2) == 0) accN[K] = padd(accN[K], v);
+                else accA[K] = padd(accA[K], v);
             };
             if ((int)xw + (int)yw + (int)zw == 1) {
                 // one flat wall (the common case): with w = (w0, w1, w2) the
@@ -454,106 +525,36 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
                     constexpr int A = 2 * K + 1, B = A + 1;
                     const int e = kd == 0 ? ev<1>(A, 0) : (kd == 1 ? ev<1>(A, 1) : ev<1>(A, 2));
                     const int away = at_hi ? -e : e;   // +1: A leaves the wall, -1: A heads into it
-                    float ta = 0.0f, tb = 0.0f;
                     if (away != 0) {
-                        const float ca = own(std::integral_constant<int, A>{});
-                        const float cb = own(std::integral_constant<int, B>{});
-                        const float ref = G::LOCAL ? 0.0f : p.ref[sp][wclass<1>(A)];
-                        if (away > 0) { ta = w2 * ca + w0 * cb + ref * w2; tb = ref * -w2; }
-                        else { ta = ref * -w2; tb = w2 * cb + w0 * ca + ref * w2; }
+                        float ca = tile_center<A, NS, S, TY, SLOTS>(base, sp, tx, ty);
+                        float cb = tile_center<B, NS, S, TY, SLOTS>(base, sp, tx, ty);
+                        float ref = 0.0f;
+                        if constexpr (G::LOCAL) {   // decoded with the node's density
+                            ca = fmaf(p.wl[wclass<1>(A)], rd[1][1], ca);
+                            cb = fmaf(p.wl[wclass<1>(A)], rd[1][1], cb);
+                        } else {
+                            ref = p.ref[sp][wclass<1>(A)];
+                        }
+                        const float2 t = away > 0 ? make_float2(w2 * ca + w0 * cb + ref * w2, ref * -w2)
+                                                  : make_float2(ref * -w2, w2 * cb + w0 * ca + ref * w2);
+                        add_term(kc, t);
                     }
-                    cw[A * G::threads] = ta;
-                    cw[B * G::threads] = tb;
                 });
             } else {   // edges and corners: the host table of the wall class
                 const int zc_next = zwall ? (k == 0 ? 1 : (k == p.nz - 1 ? 2 : 0)) : 0;
-                const float4* L = lumps + ((wcls_xy + 9 * zc_next) * NS + sp) * Q;
+                float t[18];
+                wall_terms_table<NS, S, TY, SLOTS>(base, sp, tx, ty, lumps + ((wcls_xy + 9 * zc_next) * NS + sp) * Q,
+                                                   p.ref[sp][1], p.ref[sp][2], p.wl[1], p.wl[2], rd[1][1], t);
                 static_for<0, NP>([&](auto kc) {
                     constexpr int K = decltype(kc)::value;
-                    constexpr int A = 2 * K + 1, B = A + 1;
-                    const float4 la = __ldg(L + A), lb = __ldg(L + B);
-                    const float ca = own(std::integral_constant<int, A>{});
-                    const float cb = own(std::integral_constant<int, B>{});
-                    const float ref = G::LOCAL ? 0.0f : p.ref[sp][wclass<1>(A)];
-                    cw[A * G::threads] = la.x * ca + la.y * cb + ref * la.z;
-                    cw[B * G::threads] = lb.x * cb + lb.y * ca + ref * lb.z;
+                    add_term(kc, make_float2(t[2 * K], t[2 * K + 1]));
                 });
             }
-        }
-        float f0;
-        float2 F[NP];
-        if (ok && unit) {
-            // exact shift: each member reads its upstream node; a z-moving
-            // member bound for +z takes slab z - 1 (two iterations ago, held
-            // in the shift register accB -> accA), one bound for -z slab z + 1
-            f0 = accN0;
-            if (!halo) accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1][1], p.wl[0]);
-            static_for<0, NP>([&](auto kc) {
-                constexpr int K = decltype(kc)::value;
-                constexpr int A = 2 * K + 1, B = A + 1;
-                constexpr int ez = ev<1>(A, 2);
-                const float wa = p.wl[wclass<1>(A)];
-                const float dA = rd[1 - ev<1>(A, 1)][1 - ev<1>(A, 0)], dB = rd[1 - ev<1>(B, 1)][1 - ev<1>(B, 0)];
-                if constexpr (ez == 0) {
-                    F[K] = accN[K];
-                    if (!halo)
-                        accN[K] = make_float2(inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa),
-                                              inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa));
-                } else if constexpr (ez > 0) {   // A bound for +z, B for -z
-                    F[K].x = accA[K].x;
-                    accA[K].x = accB[K].x;
-                    accB[K].x = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa);
-                    F[K].y = inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa);
-                } else {                         // A bound for -z, B for +z
-                    F[K].y = accA[K].y;
-                    accA[K].y = accB[K].y;
-                    accB[K].y = inplane_unit<B, NS, S, TY, SLOTS>(base, sp, tx, ty, dB, wa);
-                    F[K].x = inplane_unit<A, NS, S, TY, SLOTS>(base, sp, tx, ty, dA, wa);
-                }
-            });
-        } else if (ok) {
-            float di[3][3] = {};   // [ey + 1][ex + 1]
-            if constexpr (G::LOCAL)
-                static_for<0, 9>([&](auto kc) {
-                    constexpr int K = decltype(kc)::value;
-                    di[K / 3][K % 3] = dens_interp<K % 3 - 1, K / 3 - 1>(rd, w);
-                });
-            f0 = accN0;
-            if (!halo) {
-                if constexpr (G::LOCAL) accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, rd[1][1], p.wl[0]);
-                else accN0 = inplane_unit<0, NS, S, TY, SLOTS>(base, sp, tx, ty, 0.0f, 0.0f);
-            }
-            static_for<0, NP>([&](auto kc) {
-                constexpr int K = decltype(kc)::value;
-                constexpr int A = 2 * K + 1;
-                constexpr int ex = ev<1>(A, 0), ey = ev<1>(A, 1), ez = ev<1>(A, 2);
-                const float wa = p.wl[wclass<1>(A)];
-                const float2 dI = make_float2(di[ey + 1][ex + 1], di[1 - ey][1 - ex]);
-                if constexpr (ez == 0) {
-                    F[K] = accN[K];
-                    if (!halo) accN[K] = inplane2<A, NS, S, TY, SLOTS>(base, sp, tx, ty, wp, dI, wa);
-                } else {
-                    const float2 R = inplane2<A, NS, S, TY, SLOTS>(base, sp, tx, ty, wp, dI, wa);
-                    // slab k feeds the nodes at z = k+1 (oz=-1), k (0), k-1 (+1)
-                    F[K] = pfma(wpo<ez>(wp, 1), R, accA[K]);
-                    accA[K] = pfma(wpo<ez>(wp, 0), R, accB[K]);
-                    accB[K] = pmul(wpo<ez>(wp, -1), R);
-                }
-            });
         }
 
-        // ---- node (x, y, zo): wall terms, correction, moments
+        // ---- node (x, y, zo): correction, moments
         float rho = 1.0f, drho = 0.0f, ueq[3] = {0.0f, 0.0f, 0.0f};
         if (ok && emit) {
-            if (wall_node) {   // the App. A terms computed last iteration
-                const float* cs =
-                    reinterpret_cast<const float*>(smem + G::cen_offset) + ((idx - 1) & 1) * Q * G::threads + threadIdx.x;
-                static_for<0, NP>([&](auto kc) {
-                    constexpr int K = decltype(kc)::value;
-                    constexpr int A = 2 * K + 1;
-                    F[K] = padd(F[K], make_float2(cs[A * G::threads], cs[(A + 1) * G::threads]));
-                });
-            }
             // moments from the pairs: s = f_A + f_B adds to rho, d = f_A - f_B
             // to the momentum along A's components (sums start from a term)
             float r = f0, j[3];
