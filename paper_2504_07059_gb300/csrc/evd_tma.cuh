@@ -438,7 +438,6 @@ k_step_tma(const __grid_constant__ TmaMaps maps, const Params<float> p, const S*
         const bool halo = stage_is_halo(k, zb, ze);
         const int zo = k - 1;                   // node finished this iteration
         const bool emit = zo >= zb && zo < ze;  // the same for every thread of the CTA
-        const bool zlo = zwall && zo == 0, zhi = zwall && zo == p.nz - 1;
         const int node = x + p.nx * y + nxy * zo;
         // the node of this stage's slab, finished next iteration, at a wall
         const bool wall_next = !halo && active && (col_wall || (zwall && (k == 0 || k == p.nz - 1)));
