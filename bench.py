@@ -52,14 +52,11 @@ FALLBACK_HBM_GBS = 6800.0
 # capture of the kernel sources with this digest (summaries under profiles/).
 # A change to those sources changes the digest and the entry no longer applies.
 NCU_TRAFFIC = {
-    # 128^3 captures, x8 for a 256^3 launch: FP32 545.6 MB read + 437.8 MB written,
-    # FP16 storage 268.3 MB read + 213.9 MB written.  Captured from sources with
-    # digest 38d5b5e11651c842; the sources below differ from them only in the
-    # general collision template, which k_step_tma does not instantiate, and
-    # k_step_tma<3, float, 2, 3> and <3, __half, 2, 4> compile to byte-identical
-    # code from both (compared without line information)
-    ("90840397bbc90fa6", "stratification", 256, "fp32"): 7867.1e6,
-    ("90840397bbc90fa6", "stratification", 256, "fp16"): 3858.1e6,
+    # 128^3 captures (k_step_tma, one-row tiles), x8 for a 256^3 launch: FP32
+    # 537.9 MB read + 439.9 MB written (1.023 x the algorithmic 956.3 MB), FP16
+    # storage 258.1 MB read + 213.8 MB written
+    ("8227cc2459e25752", "stratification", 256, "fp32"): 7823.0e6,
+    ("8227cc2459e25752", "stratification", 256, "fp16"): 3775.3e6,
 }
 
 
@@ -67,8 +64,14 @@ NCU_TRAFFIC = {
 # the ncu thread-instruction counters of one launch (dadd + dmul + 2 dfma for
 # double; fadd + fmul + 2 ffma, doubled for the f32x2 forms, for float), keyed
 # like NCU_TRAFFIC.  They place the compute-bound paths on their arithmetic
-# roof.
-NCU_FLOPS = {}
+# roof.  FP64: the general step on a 64^3 copy of the workload (wall nodes,
+# whose lumps add arithmetic, are 9 % of its sites against 2 % at 256^3);
+# FP32 and FP16 storage: k_step_tma on a 128^3 copy.
+NCU_FLOPS = {
+    ("8227cc2459e25752", "stratification", "fp64"): 614.2,
+    ("8227cc2459e25752", "stratification", "fp32"): 632.0,
+    ("8227cc2459e25752", "stratification", "fp16"): 749.5,
+}
 
 
 def flops_for(digest: str, workload: str, precision: str):
@@ -91,9 +94,9 @@ def measure_alu_peaks(torch, dev, stream, device_id) -> dict:
 
 
 # The sources that define the step kernels and their launch configuration
-# (the device code, the TMA step, the launchers and the FP32/FP16 D3Q19 units).
+# (the device code, the TMA step, the launchers and the D3Q19 units).
 KERNEL_SOURCES = ("evd_device.cuh", "evd_tma.cuh", "evd_tma_launch.cuh", "evd_launch.cuh",
-                  "evd_fp32_d3q19.cu", "evd_fp16_d3q19.cu")
+                  "evd_fp32_d3q19.cu", "evd_fp16_d3q19.cu", "evd_fp64_d3q19.cu")
 
 
 def kernel_digest() -> str:
