@@ -501,7 +501,8 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
         print(json.dumps(out), flush=True)
 
 
-def measure_single(torch, dev, stream, wl, prec: str, x_dev, steps: int, warmup: int) -> dict:
+def measure_single(torch, dev, stream, wl, prec: str, x_dev, steps: int, warmup: int,
+                   workload: str = "", size: int = 0) -> dict:
     """One lattice in another storage: CUDA-event time per step over ``steps``
     steps after ``warmup``, the roofline of its step kernel (algorithmic bytes
     of that storage) and the kernel that ran."""
@@ -526,7 +527,8 @@ def measure_single(torch, dev, stream, wl, prec: str, x_dev, steps: int, warmup:
             "steps": steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind, "kernel": kernel,
-                         "bytes_per_launch": bpl}}
+                         "bytes_per_launch": bpl,
+                         "traffic": traffic_for(kernel_digest(), workload, size, prec) if kernel == "k_step_tma" else None}}
 
 
 def run_adjoint(args, torch, dev) -> None:
@@ -733,7 +735,8 @@ def run_ours(args) -> None:
     # in FP32 with its FP64 batch beside it
     extras = {}
     if not args.no_extras and args.workload == "stratification" and prec == "fp32":
-        extras["fp16"] = measure_single(torch, dev, stream, wl, "fp16", x_dev, min(args.steps, 300), 5)
+        extras["fp16"] = measure_single(torch, dev, stream, wl, "fp16", x_dev, min(args.steps, 300), 5,
+                                        args.workload, args.size)
         if fp64 is not None:
             extras["fp16"]["speedup_over_fp64"] = fp64["ms_per_step"] / extras["fp16"]["ms_per_step"]
             f32 = flops_for(kernel_digest(), args.workload, "fp16")

@@ -122,3 +122,12 @@ def test_species_limits_per_lattice(evd):
     M = [1.0, 2.0, 3.0, 4.0]
     sp = evd.SpeciesTable(M, np.full((4, 4), 0.05), 1.0, flags=evd.EVD_FORCE_S_DIFF)
     assert evd.evd_required_bytes(evd.make_grid(evd.EVD_D2Q9, evd.EVD_FP64, (6, 8), 0), sp) == 0
+
+
+def test_fma_rate_validates_its_arguments_before_any_cuda_call(evd):
+    """The arithmetic-roof microbenchmark rejects an unknown kind and an
+    iteration count out of range with EVD_ERR_ARG (no device needed)."""
+    for kind, iters in ((3, 16), (-1, 16), (0, 0), (1, 1 << 25)):
+        with pytest.raises(evd.EVDError) as ei:
+            evd.evd_fma_rate(kind, iters)
+        assert ei.value.status == evd.EVD_ERR_ARG

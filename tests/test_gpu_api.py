@@ -143,3 +143,20 @@ def test_launch_count_accounts_for_every_kernel(evd):
     # 16 step kernels + 4 mass-correction reductions
     assert evd.evd_launch_count(sim.ctx) - n0 == 20
     sim.close()
+
+
+def test_fma_rate_measures_the_arithmetic_roofs(evd):
+    """evd_fma_rate (the FMA chains behind the bench's arithmetic roofs):
+    positive rates, double below float by the GPU's FP64 ratio, and the
+    counted operations those of the launch (2 per FMA, 8 chains, 8 blocks of
+    256 threads per SM)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rates = {}
+    for kind in (0, 1, 2):
+        flops, ms = evd.evd_fma_rate(kind, 1 << 12)
+        per_thread = 2 * 8 * (1 << 12) * (2 if kind == 2 else 1)
+        assert flops == per_thread * 8 * 256 * sms
+        assert ms > 0.0
+        rates[kind] = flops / ms
+    assert rates[1] > 8 * rates[0]
