@@ -53,8 +53,14 @@ typedef struct {
 
 /* Creates a batch of n_members >= 1 members of one lattice (EVD_D2Q9 or
  * EVD_D3Q19) and one precision (EVD_FP64, EVD_FP32, EVD_FP16_STORE) on the
- * current device.  Allocates two population buffers holding every member
- * (each member's planes padded to 64 elements) plus small tables.
+ * current device.  Reduced storage keeps deviations from each node's own
+ * density (EVD_FP32: in the rest plane, as evd_set_reference_mode's
+ * EVD_REF_NODE; EVD_FP16_STORE: in an extra half plane) and rounds its last
+ * operation with a dither seeded per step from a device step counter (so
+ * graph replays draw fresh seeds; evd_batch_set_fields resets it and
+ * evd_batch_autotune restores it).  Allocates two population buffers holding
+ * every member (each member's planes padded to 64 elements) plus small
+ * tables.
  * EVD_ERR_ARG if a member is invalid (the message names it), EVD_ERR_CUDA if
  * an allocation fails.  *out is NULL on failure. */
 evd_status evd_batch_create(int lattice, int precision, const evd_member* members, int n_members,
