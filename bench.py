@@ -57,6 +57,9 @@ NCU_TRAFFIC = {
     # storage 258.1 MB read + 213.8 MB written
     ("8227cc2459e25752", "stratification", 256, "fp32"): 7823.0e6,
     ("8227cc2459e25752", "stratification", 256, "fp16"): 3775.3e6,
+    # the batched sweep: k_step_batch on the first 64 tubes, 204.5 MB read + 180.2 MB written
+    # = 0.99943 x the algorithmic 384.9 MB, the same ratio applied to the 512-tube launch
+    ("324794d064f54151", "tubes", 512, "fp32"): 3461.8e6,
 }
 
 
@@ -99,9 +102,13 @@ KERNEL_SOURCES = ("evd_device.cuh", "evd_tma.cuh", "evd_tma_launch.cuh", "evd_la
                   "evd_fp32_d3q19.cu", "evd_fp16_d3q19.cu", "evd_fp64_d3q19.cu")
 
 
-def kernel_digest() -> str:
+# The sources of the batched step kernel (FP32 D2Q9 storage).
+BATCH_SOURCES = ("evd_device.cuh", "evd_batch_kernels.cuh", "evd_batch_fp32_d2q9.cu")
+
+
+def kernel_digest(sources: tuple = KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2504_07059_gb300", "csrc", name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -483,7 +490,8 @@ def run_tubes(args, torch, dev, world, rank, local) -> None:
             "config": dict(tubes_config(args.members), precision=prec, parallelism=f"replicas{world}",
                            schedule=r["schedule"], graph_steps=8, l2="inputs larger than L2 (no flush needed)"),
             "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
-                         "frac": r["frac"], "traffic": None, "peak_source": r["peak_source"],
+                         "frac": r["frac"], "traffic": traffic_for(kernel_digest(BATCH_SOURCES), "tubes", args.members, prec),
+                         "peak_source": r["peak_source"],
                          "kernel": "k_step_batch", "bytes_per_launch": r["bytes_per_launch"],
                          "timing": "CUDA events around the timed steps, divided by the steps "
                                    "(includes the small mass-correction reductions)"},
@@ -750,7 +758,8 @@ def run_ours(args) -> None:
                            "ms_per_step": r["ms_per_step"], "value": r["value"], "unit": UNIT,
                            "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
                                         "unit": "GB/s", "frac": r["frac"], "kernel": "k_step_batch",
-                                        "bytes_per_launch": r["bytes_per_launch"]},
+                                        "bytes_per_launch": r["bytes_per_launch"],
+                                        "traffic": traffic_for(kernel_digest(BATCH_SOURCES), "tubes", 512, "fp32")},
                            "schedule": r["schedule"], "graph_steps": 8,
                            "fp64_ms_per_step": r["fp64"]["ms_per_step"], "speedup_over_fp64": r["fp64"]["speedup"],
                            "config": tubes_config()}

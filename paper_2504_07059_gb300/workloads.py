@@ -233,6 +233,13 @@ TUBE_BELOW = {2: (0.9, 0.1), 3: (0.7, 0.2, 0.1)}   # mole fractions in the lower
 TUBE_ABOVE = {2: (0.1, 0.9), 3: (0.1, 0.2, 0.7)}   # and in the upper half
 
 
+def tube_length_and_species(k: int, lmin: int = 128, lmax: int = 4096, seed: int = SEED) -> tuple:
+    """Length L and species count of tube k of the sweep below (the first two
+    draws of its stream), without building its fields."""
+    u = uniform01(1000 + 4 * k, 2, seed)
+    return int(round(lmin * (lmax / lmin) ** u[0])), (2 if u[1] < 0.5 else 3)
+
+
 def batched_tubes(count: int = 512, width: int = 32, lmin: int = 128, lmax: int = 4096,
                   steps: int = 10000, seed: int = SEED, width_interface: float = 0.0) -> list:
     """A sweep of independent D2Q9 Loschmidt tubes (periodic across the width,
@@ -251,8 +258,7 @@ def batched_tubes(count: int = 512, width: int = 32, lmin: int = 128, lmax: int 
     for k in range(count):
         base = 1000 + 4 * k
         u = uniform01(base, 5, seed)
-        L = int(round(lmin * (lmax / lmin) ** u[0]))
-        ns = 2 if u[1] < 0.5 else 3
+        L, ns = tube_length_and_species(k, lmin, lmax, seed)
         r = 1.0 + 9.0 * u[2]
         M = (1.0, r) if ns == 2 else (1.0, 1.0 + (r - 1.0) * u[3], r)
         g = 5e-6 * u[4]

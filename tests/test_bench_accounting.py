@@ -26,12 +26,26 @@ def test_algorithmic_bytes_per_update():
 
 def test_traffic_entries_are_plausible_and_keyed_to_kernel_sources():
     """Every captured traffic entry is within 10 % of the algorithmic bytes of
-    its workload, and the lookup the bench makes gives nothing for sources
-    that were not captured (a changed kernel reports traffic null)."""
+    its workload (the 256^3 box, or the batched sweep: 2 Q b per
+    species-site update of every tube), and the lookup the bench makes gives
+    nothing for sources that were not captured (a changed kernel reports
+    traffic null)."""
     assert bench.NCU_TRAFFIC
     for (digest, workload, size, prec), t in bench.NCU_TRAFFIC.items():
-        assert len(digest) == 16 and workload == "stratification"
-        algorithmic = bench.bytes_per_ssu(W.stratification_3d(n=8), prec) * 3 * size ** 3
-        assert 0.9 < t / algorithmic < 1.1, (digest, prec, t / algorithmic)
+        assert len(digest) == 16 and workload in ("stratification", "tubes")
+        if workload == "stratification":
+            algorithmic = bench.bytes_per_ssu(W.stratification_3d(n=8), prec) * 3 * size ** 3
+        else:
+            per = bench.bytes_per_ssu(W.loschmidt_binary(nx=4, ny=16), prec)   # D2Q9: 2 x 9 x b
+            algorithmic = sum(ns * 32 * L * per for L, ns in (W.tube_length_and_species(k) for k in range(size)))
+        assert 0.9 < t / algorithmic < 1.1, (digest, workload, prec, t / algorithmic)
     assert bench.traffic_for("0" * 16, "stratification", 256, "fp32") is None
     assert len(bench.kernel_digest()) == 16
+    assert len(bench.kernel_digest(bench.BATCH_SOURCES)) == 16
+
+
+def test_tube_shapes_match_the_sweep():
+    """The shape helper draws the same lengths and species counts as the sweep."""
+    tubes = W.batched_tubes(count=12)
+    for k, t in enumerate(tubes):
+        assert W.tube_length_and_species(k) == (t.shape[1], t.ns)
